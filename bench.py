@@ -1,0 +1,464 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the accelerated FBP (IIR ramp filter + fast Hough transform
+back projection) on GB300.
+
+One step = the whole method (recursive filtering, resampling fused with the first Hough
+pass, second Hough pass fused with the quarter sum) over a stack of 64 slices of N = 2048
+(K = 3072 angles, M = 2897 bins) per GPU, synthetic noisy ten-ellipse phantoms, with the
+sinograms already resident in HBM.  The stack (2.28 GB of sinograms) is larger than L2, so
+no flush is needed between steps.
+
+Printed (rank 0, one JSON line): slices/s of the whole job, the event-timed roofline of
+the dominant kernel, the end-to-end number through the host-memory entry point, the
+direct GPU FBP comparator, the RMSE against the float64 direct reconstruction at sampled
+pixels, the SM clocks seen during the timed region and the CPU oracle baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+With N > 1 run it under torch.distributed.run: every rank reconstructs its own stack
+(independent slices, no collective on the data path), timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "slices/s at N=2048 (IIR+FHT vs direct GPU FBP), %HBM roofline, RMSE vs FP64"
+UNIT = "slices/s"
+BASE_SEED = 2021
+I0 = 1e5
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--N", type=int, default=2048)
+    ap.add_argument("--slices", type=int, default=64, help="slices per GPU per step")
+    ap.add_argument("--order", type=int, default=3, help="recursive filter order Q = Mb")
+    ap.add_argument("--direct-slices", type=int, default=2)
+    ap.add_argument("--sample-pixels", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ----------------------------------------------------------------------------- topology
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def shard(rank: int, slices_per_rank: int):
+    """Global slice indices and phantom seeds of this rank's stack (weak scaling: every
+    rank owns a disjoint block of slices_per_rank consecutive slices)."""
+    first = rank * slices_per_rank
+    idx = list(range(first, first + slices_per_rank))
+    return idx, [BASE_SEED + g for g in idx]
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max over ranks (identity at world size 1)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- model
+def g_needed_floats(N: int, n1: int) -> int:
+    """Floats of the first-pass output that the second pass reads, per quarter:
+    sum over blocks bi and slopes tau of (N + (tau + 1) bi) columns."""
+    R1 = 1 << n1
+    nb = N // R1
+    if nb == 1:
+        return N * N
+    return N * N + (R1 * (R1 + 1) // 2) * (nb * (nb - 1) // 2)
+
+
+def byte_model(N: int, K: int, M: int, n1: int) -> dict:
+    """Algorithmic bytes per slice.  S, Lin, Img as in the pass-plan model
+    B_model = 3S + (2P+1) Lin + Img with P = ceil(log2 N / 6); per kernel, each kernel's
+    inputs read once and outputs written once."""
+    S = 4 * K * M
+    Lin = 32 * N * N
+    Img = 4 * N * N
+    P = math.ceil(math.log2(N) / 6)
+    G = 4 * 4 * g_needed_floats(N, n1)
+    return dict(S=S, Lin=Lin, Img=Img, P=P, B_model=3 * S + (2 * P + 1) * Lin + Img,
+                compulsory=S + Img, iir=2 * S, pass1_resample=S + G, pass2=G + Img, G=G)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = list(csv.reader(io.StringIO(open(self.path).read())))
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            r = [v.strip() for v in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle leg
+def oracle_sample(sino64, N, b, a, taus_per_quarter, ys=None, xs=None, rows=None):
+    """Time the CPU oracle, as it stands, on a bounded sample of one slice and extrapolate
+    to seconds per slice: float64 recursive filtering of `rows` projection rows (all if
+    None), float64 linogram of all four quarters, float64 dyadic-pattern back projection of
+    `taus_per_quarter` slope rows per quarter.  Optionally also evaluates the float64 fast
+    and direct reconstructions at pixels (ys, xs) for the quality figures."""
+    import numpy as np
+
+    import oracle
+    K, M = sino64.shape
+    out = {}
+    sel = sino64 if rows is None else sino64[:rows]
+    t0 = time.perf_counter()
+    pt = oracle.iir_filter(sel, b, a)
+    t_iir = (time.perf_counter() - t0) * (K / sel.shape[0])
+    if rows is not None:
+        pt = np.concatenate([pt, np.zeros((K - sel.shape[0], M))])   # timing only
+    t0 = time.perf_counter()
+    L = oracle.linogram(pt, N)
+    t_lin = time.perf_counter() - t0
+    taus = np.linspace(0, N - 1, taus_per_quarter).astype(int)
+    t0 = time.perf_counter()
+    for q in range(4):
+        oracle.pattern_backproject(L[q], taus)
+    t_bp = (time.perf_counter() - t0) * (N / taus_per_quarter)
+    del L
+    out["sec_per_slice"] = t_iir + t_lin + t_bp
+    out["work_sec"] = None
+    if ys is not None:
+        full_pt = pt if rows is None else oracle.iir_filter(sino64, b, a)
+        out["fast64"] = oracle.fast_fbp_pixels(sino64, N, b, a, ys, xs, pt=full_pt)
+        out["direct64"] = oracle.direct_fbp_pixels(sino64, N, ys, xs)
+    return out
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------------------- traffic
+def traffic_for(kernel: str):
+    """ncu DRAM bytes per launch recorded in profiles/traffic.json for `kernel`, or None if
+    absent or if the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2007_06289_gb300", "csrc", rec["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec["bytes_per_launch"] if sha == rec["source_sha256_16"] else None
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import phantoms
+    from paper_2007_06289_gb300 import binding as fbp
+    from paper_2007_06289_gb300 import build, iir_fit
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    fbp.load_library()
+
+    N, S = args.N, args.slices
+    K, M = phantoms.geometry_for(N)
+    b, a = iir_fit.coefficients(N, args.order)
+    idx, seeds = shard(rank, S)
+    sino = torch.empty((S, K, M), dtype=torch.float32, device=dev)
+    for j, sd in enumerate(seeds):
+        sino[j] = phantoms.ellipse_sinogram_torch(phantoms.random_ellipses(sd), N, K, M, dev,
+                                                  I0, sd * 7919 + 1).float()
+    plan = fbp.fbp_plan(N, K, M, S, (list(b), list(a)))
+    img = torch.empty(plan.img_shape, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        fbp.fbp_reconstruct(plan, sino, img)
+    torch.cuda.synchronize(dev)
+
+    # ---- timed region: K steps, per-kernel CUDA events recorded by the library
+    fbp.fbp_profile_enable(plan, True)
+    fbp.fbp_profile_reset(plan)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        fbp.fbp_reconstruct(plan, sino, img)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+    ms_step = reduce_max(e0.elapsed_time(e1) / args.steps, world, dev)
+    prof = fbp.fbp_profile_read(plan)
+    fbp.fbp_profile_enable(plan, False)
+    launches = sum(n for _, n in prof.values())
+
+    # ---- end to end through the host-memory entry point (pinned buffers)
+    h_sino = sino.cpu().pin_memory()
+    h_img = torch.empty(plan.img_shape, dtype=torch.float32, pin_memory=True)
+    fbp.fbp_reconstruct_host(plan, h_sino, h_img)
+    torch.cuda.synchronize(dev)
+    e2e_steps = max(1, min(args.steps, 5))
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        fbp.fbp_reconstruct_host(plan, h_sino, h_img)
+    f1.record(stream)
+    f1.synchronize()
+    ms_e2e = reduce_max(f0.elapsed_time(f1) / e2e_steps, world, dev)
+    same = bool(torch.equal(h_img, img.cpu()))
+
+    # ---- direct GPU FBP comparator on a few slices of the same stack
+    D = args.direct_slices
+    dplan = fbp.fbp_plan(N, K, M, D)
+    dimg = torch.empty(dplan.img_shape, device=dev)
+    dsino = sino[:D].contiguous()
+    fbp.fbp_direct_reconstruct(dplan, dsino, dimg)
+    torch.cuda.synchronize(dev)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(2):
+        fbp.fbp_direct_reconstruct(dplan, dsino, dimg)
+    g1.record(stream)
+    g1.synchronize()
+    ms_direct = g0.elapsed_time(g1) / 2
+    dev_err = fbp.fbp_last_device_error(plan)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+        return None
+
+    # ---- numbers
+    total_slices = S * world
+    value = total_slices / (ms_step / 1e3)
+    model = byte_model(N, K, M, plan.fuse_k)
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    per_launch_slices = plan.chunk
+    kern = {}
+    for name in ("iir", "pass1_resample", "pass2"):
+        ms, n = prof[name]
+        if n:
+            kern[name] = dict(ms_per_launch=ms / n, launches=n,
+                              bytes_per_launch=model[name] * per_launch_slices)
+    dom = max(kern, key=lambda k: kern[k]["ms_per_launch"] * kern[k]["launches"])
+    dk = kern[dom]
+    achieved = dk["bytes_per_launch"] / (dk["ms_per_launch"] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
+                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic_for(dom),
+                "peak_source": peak_src,
+                "kernels": {k: {"ms_per_launch": round(v["ms_per_launch"], 5),
+                                "launches": v["launches"],
+                                "GB_per_s": round(v["bytes_per_launch"] / (v["ms_per_launch"] / 1e3) / 1e9, 1)}
+                            for k, v in kern.items()}}
+    t_slice = ms_step / 1e3 / S
+    pipeline = {"B_model_bytes_per_slice": model["B_model"],
+                "frac_B_model_of_peak": round(model["B_model"] / (hbm * 1e9) / t_slice, 4),
+                "compulsory_bytes_per_slice": model["compulsory"],
+                "frac_compulsory_of_peak": round(model["compulsory"] / (hbm * 1e9) / t_slice, 4)}
+
+    # quality at sampled pixels of slice 0, and the CPU oracle baseline (one leg)
+    rng = np.random.default_rng(0)
+    P = args.sample_pixels
+    ys, xs = rng.integers(0, N, P), rng.integers(0, N, P)
+    fast_img = img[0].cpu().numpy()
+    dir_img = dimg[0].cpu().numpy()
+    truth = phantoms.ellipse_image(phantoms.random_ellipses(seeds[0]), N)
+    quality = {"pixels": P,
+               "rmse_fast_vs_phantom": float(np.sqrt(np.mean((fast_img - truth) ** 2))),
+               "rmse_direct_vs_phantom": float(np.sqrt(np.mean((dir_img - truth) ** 2)))}
+    cpu_baseline = None
+    if not args.no_cpu_baseline:
+        s64 = sino[0].cpu().numpy().astype(np.float64)
+        t0 = time.perf_counter()
+        res = oracle_sample(s64, N, b, a, taus_per_quarter=8, ys=ys, xs=xs)
+        work = time.perf_counter() - t0
+        f64, d64 = res["fast64"], res["direct64"]
+        rng_img = float(fast_img.max() - fast_img.min())
+        quality.update({
+            "rmse_fast_vs_fp64_direct": float(np.sqrt(np.mean((fast_img[ys, xs] - d64) ** 2))),
+            "rmse_direct_gpu_vs_fp64_direct": float(np.sqrt(np.mean((dir_img[ys, xs] - d64) ** 2))),
+            "rmse_fp64_fast_vs_fp64_direct": float(np.sqrt(np.mean((f64 - d64) ** 2))),
+            "max_abs_vs_fp64_fast_over_range": float(np.abs(fast_img[ys, xs] - f64).max() / rng_img),
+        })
+        cpu_baseline = {"value": round(1.0 / res["sec_per_slice"], 6), "unit": UNIT,
+                        "cores": 1, "kind": "oracle",
+                        "sample": ("one N=2048 slice: float64 recursive filter of all 3072 rows, "
+                                   "float64 linogram of all four quarters, float64 dyadic-pattern "
+                                   "back projection of 8 of 2048 slopes per quarter (scaled x256); "
+                                   f"host has {cpu_cores()} cores, numpy runs single-threaded"),
+                        "work_seconds": round(work, 1)}
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: seeded ten-ellipse phantoms, closed-form Radon transform, Poisson noise I0=1e5",
+        "config": {"workload": f"N={N} K={K} M={M} stack of {S} noisy ellipse-phantom slices per GPU",
+                   "N": N, "K": K, "M": M, "slices_per_gpu": S, "iir_order": args.order,
+                   "fuse_k": plan.fuse_k, "chunk": plan.chunk,
+                   "l2": "no flush: the per-step sinogram stack (%.2f GB) is larger than L2"
+                         % (S * K * M * 4 / 1e9)},
+        "voxels_per_s": round(value * N * N, 1),
+        "roofline": roofline,
+        "pipeline_roofline": pipeline,
+        "e2e": {"value": round(total_slices / (ms_e2e / 1e3), 2), "unit": UNIT,
+                "h2d_bytes_per_step": S * K * M * 4, "d2h_bytes_per_step": S * N * N * 4,
+                "api": "fbp_reconstruct_host (pinned host buffers)", "matches_device_result": same},
+        "gpu_launches": launches,
+        "direct_gpu": {"value": round(D / (ms_direct / 1e3), 3), "unit": UNIT, "slices": D,
+                       "speedup_fast_over_direct": round((S / ms_step) / (D / ms_direct), 1)},
+        "quality": quality,
+        "clocks": clocks,
+        "cpu_baseline": cpu_baseline,
+        "device_status": dev_err,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+    return line
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The CPU oracle as the reference arm: each step times a bounded sample of one slice
+    of the same workload (float64 recursive filter of 192 of 3072 rows, float64 linogram,
+    dyadic-pattern back projection of 2 slopes per quarter) and extrapolates to slices/s."""
+    import numpy as np
+
+    import phantoms
+    from paper_2007_06289_gb300 import iir_fit
+
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    N = args.N
+    K, M = phantoms.geometry_for(N)
+    b, a = iir_fit.coefficients(N, args.order)
+    sd = BASE_SEED
+    s64 = phantoms.ellipse_sinogram(phantoms.random_ellipses(sd), N, K, M, I0, sd * 7919 + 1)
+    for _ in range(args.warmup):
+        oracle_sample(s64, N, b, a, taus_per_quarter=2, rows=192)
+    secs = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        secs.append(oracle_sample(s64, N, b, a, taus_per_quarter=2, rows=192)["sec_per_slice"])
+    wall = time.perf_counter() - t0
+    v = 1.0 / statistics.mean(secs)
+    sample = ("per step, one N=2048 slice: float64 recursive filter of 192 of 3072 rows (x16), "
+              "float64 linogram of all four quarters, float64 dyadic-pattern back projection of "
+              "2 of 2048 slopes per quarter (x1024)")
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(wall / args.steps * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"N={N} K={K} M={M} noisy ellipse-phantom slices", "N": N,
+                       "K": K, "M": M, "iir_order": args.order},
+            "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * fbp.h - C ABI of the GB300 library for accelerated filtered back projection
+ * (IIR ramp filtering + fast Hough transform back projection; Dolmatova, Chukalina and
+ * Nikolaev, "Accelerated FBP for computed tomography image reconstruction",
+ * arXiv 2007.06289).
+ *
+ * Data (all float32, row-major, C order):
+ *   sinogram  [count][K][M]    angle theta_k = k*pi/K, detector offset r_m = m - (M-1)/2
+ *                              pixels; a value is the line integral over
+ *                              {(x-c0) cos(theta) + (y-c0) sin(theta) = r}, c0 = (N-1)/2
+ *   filtered  [count][K][M]    the ramp-filtered sinogram (Eq. 12)
+ *   linogram  [count][4][N][2N] quarters in the order v-, v+, h-, h+ (Sec. 4.1); row i holds
+ *                              lines of slope sigma_i = i/(N-1); column c holds intercept
+ *                              u = c (v-, h-) or u = N-1-c (v+, h+); rows are pre-weighted
+ *   image     [count][N][N]    f[y][x], pixel centres at integer (x, y)
+ *
+ * Conventions shared by every call:
+ *   - N is a power of two with 2 <= N <= 4096; K >= 2 and M >= 2 are free.
+ *   - Device pointers are owned by the caller, must be 16-byte aligned (else
+ *     FBP_ERR_MISALIGNED) and must not overlap unless a call says so.  Rows need not be
+ *     aligned.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the legacy default
+ *     stream).  Arguments are validated before anything is launched; a call that returns
+ *     an error has launched nothing.  A CUDA launch failure returns FBP_ERR_CUDA.
+ *   - A plan is not thread-safe: calls on one plan must be issued from one host thread.
+ *     Calls that use the plan's workspace must not overlap on the GPU (issue them on one
+ *     stream, or order them with events).
+ *   - No call throws; no call synchronises the device except fbp_plan_destroy and
+ *     fbp_last_device_error.
+ */
+#ifndef FBP_H
+#define FBP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fbp_plan_s* fbp_plan_t;
+
+typedef enum {
+    FBP_OK = 0,
+    FBP_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad coefficient set */
+    FBP_ERR_UNSUPPORTED = 2,   /* N not a power of two in [2, 4096], filter order > 8 */
+    FBP_ERR_MISALIGNED = 3,    /* a pointer is not 16-byte aligned */
+    FBP_ERR_OOM = 4,           /* device or host allocation failed */
+    FBP_ERR_CUDA = 5,          /* a CUDA runtime call or launch failed */
+    FBP_ERR_TIMEOUT = 6,       /* a bounded wait inside a kernel gave up */
+    FBP_ERR_INTERNAL = 7       /* a kernel's own consistency check failed */
+} fbp_status;
+
+#define FBP_MAX_ORDER 8
+
+/* Coefficients of the causal recursive filter of Eq. 9 / Eq. 13:
+ *   y(n) = sum_{k<mb} b[k] p(n-k) - sum_{k=1..q} a[k-1] y(n-k),
+ * used unchanged (a+ = a-, b+ = b-, text after Eq. 13) by the anticausal filter.
+ * 1 <= mb <= 8, 0 <= q <= 8; entries past mb / q are ignored.  The filter must be stable
+ * with distinct poles (roots of z^q + a[0] z^(q-1) + ... + a[q-1] strictly inside the unit
+ * circle and pairwise separated); fbp_plan checks both.
+ * The plan turns the coefficients (in float64) into the same transfer function in
+ * parallel form, sum_j r_j / (1 - p_j z^-1) plus direct taps, and the kernels run that form
+ * in float32: rounding the direct-form a[] to float32 can move poles near z = 1 outside
+ * the unit circle, while poles and residues round harmlessly. */
+typedef struct {
+    int mb;
+    int q;
+    double b[FBP_MAX_ORDER];
+    double a[FBP_MAX_ORDER];
+} fbp_iir_coeffs;
+
+/* Built-in coefficients fitted for image size N and order q = mb = `order` (2..6) by a
+ * simplex search on the weighted response error (Sec. 3, text after Eq. 13).
+ * order <= 0 selects the default order 3 (the paper's setting, Sec. 5).
+ * Errors: FBP_ERR_INVALID_ARG (out == NULL), FBP_ERR_UNSUPPORTED (no table entry). */
+fbp_status fbp_default_coeffs(int N, int order, fbp_iir_coeffs* out);
+
+/* Create a plan for slices of an N x N image from K angles x M bins, `batch` slices per
+ * call.  coeffs == NULL selects fbp_default_coeffs(N, 0).  fuse_k is the number of Hough
+ * stages done by the first back-projection pass (1..6; 0 chooses).  The plan builds its
+ * per-row geometry tables (Eq. 14-15) on the host in float64 and uploads them; it
+ * allocates no workspace yet.  The current CUDA device at creation is the plan's device.
+ * Errors: FBP_ERR_INVALID_ARG, FBP_ERR_UNSUPPORTED, FBP_ERR_OOM, FBP_ERR_CUDA. */
+fbp_status fbp_plan(fbp_plan_t* out, int N, int K, int M, int batch,
+                    const fbp_iir_coeffs* coeffs, int fuse_k);
+
+/* Synchronise the plan's device, free everything the plan owns.  NULL is accepted. */
+fbp_status fbp_plan_destroy(fbp_plan_t plan);
+
+/* Bytes of device workspace that fbp_reconstruct, fbp_fht_backproject,
+ * fbp_reconstruct_host and fbp_direct_reconstruct need (0 if plan == NULL). */
+size_t fbp_workspace_bytes(fbp_plan_t plan);
+
+/* Hand the plan a caller-owned device workspace of at least fbp_workspace_bytes bytes
+ * (16-byte aligned).  Without one the plan allocates its own on first use (cudaMalloc),
+ * which must then not happen inside a CUDA graph capture.  d_ws == NULL drops a caller
+ * workspace (the plan will allocate on next use).
+ * Errors: FBP_ERR_INVALID_ARG (too small), FBP_ERR_MISALIGNED. */
+fbp_status fbp_set_workspace(fbp_plan_t plan, void* d_ws, size_t bytes);
+
+/* Eq. 12-13: filtered = causal + anticausal recursive filtering of every projection row,
+ * zero state outside [0, M).  d_sino [batch][K][M] -> d_filt [batch][K][M]; the two may be
+ * the same buffer. */
+fbp_status fbp_filter_iir(fbp_plan_t plan, const float* d_sino, float* d_filt, void* stream);
+
+/* Sec. 4.1-4.2, Eq. 14-15: bilinear resampling of the filtered sinogram into the four
+ * weighted linogram quarters.  d_filt [batch][K][M] -> d_lin [batch][4][N][2N]; every
+ * entry of d_lin is written. */
+fbp_status fbp_resample_st(fbp_plan_t plan, const float* d_filt, float* d_lin, void* stream);
+
+/* Sec. 4.4-4.5, Eq. 16-22: fast Hough transform of every quarter along dyadic patterns and
+ * the sum of the four quarter images, (F_v- + F_v+) + (F_h- + F_h+), in float32.
+ * d_lin [batch][4][N][2N] (read only) -> d_img [batch][N][N].  Uses the workspace.
+ * Only linogram entries with column c <= N-1+i can reach the image. */
+fbp_status fbp_fht_backproject(fbp_plan_t plan, const float* d_lin, float* d_img, void* stream);
+
+/* The whole method: fbp_filter_iir, fbp_resample_st and fbp_fht_backproject composed, with
+ * the linogram never written to memory.  d_sino [batch][K][M] -> d_img [batch][N][N].
+ * The result equals the composition of the three calls bit for bit.  Uses the workspace. */
+fbp_status fbp_reconstruct(fbp_plan_t plan, const float* d_sino, float* d_img, void* stream);
+
+/* fbp_reconstruct from and to HOST memory: copies `count` slices (any count >= 1) of
+ * h_sino [count][K][M] to the device, reconstructs and copies h_img [count][N][N] back,
+ * pipelining copies and compute over chunks of slices on internal streams ordered after
+ * `stream`; `stream` is ordered after the last copy.  Host buffers should be pinned
+ * (cudaHostAlloc / cudaHostRegister) for the copies to overlap.  Uses the workspace. */
+fbp_status fbp_reconstruct_host(fbp_plan_t plan, const float* h_sino, float* h_img, int count,
+                                void* stream);
+
+/* Comparator, not the paper's method: direct Theta(N^3) FBP (Eq. 3-5 with the exact FIR
+ * ramp of Eq. 8, L0 = M-1, and pixel-driven linear-interpolation back projection,
+ * f = (pi/K) sum_k p~_k((x-c0) cos theta_k + (y-c0) sin theta_k)).
+ * d_sino [batch][K][M] -> d_img [batch][N][N].  Uses the workspace. */
+fbp_status fbp_direct_reconstruct(fbp_plan_t plan, const float* d_sino, float* d_img,
+                                  void* stream);
+
+/* Plan shape: any output pointer may be NULL. */
+fbp_status fbp_plan_info(fbp_plan_t plan, int* N, int* K, int* M, int* batch, int* fuse_k,
+                         int* chunk);
+
+/* Kernels of the library, for fbp_profile_read.  The paper has no counterpart: these are
+ * measurement hooks. */
+typedef enum {
+    FBP_KERNEL_IIR = 0,            /* recursive ramp filter (Eq. 12-13) */
+    FBP_KERNEL_RESAMPLE = 1,       /* stand-alone resampling (fbp_resample_st) */
+    FBP_KERNEL_PASS1_RESAMPLE = 2, /* resampling fused with the first Hough pass */
+    FBP_KERNEL_PASS1_LINOGRAM = 3, /* first Hough pass reading a stored linogram */
+    FBP_KERNEL_PASS2 = 4,          /* second Hough pass fused with the quarter sum */
+    FBP_KERNEL_FIR = 5,            /* comparator: exact FIR ramp */
+    FBP_KERNEL_DIRECT_BP = 6,      /* comparator: pixel-driven back projection */
+    FBP_KERNEL_COUNT = 7
+} fbp_kernel_id;
+
+/* Measurement hooks (no counterpart in the paper).  The plan always counts the kernels it
+ * launches.  With profiling enabled it also records a pair of CUDA events around every
+ * launch, on the stream the kernel is launched on (events are created lazily, so enable
+ * profiling outside any CUDA graph capture).  fbp_profile_read synchronises on the last
+ * recorded event and returns, for one kernel id, the summed event-timed duration in ms and
+ * the number of launches since the last reset.  fbp_profile_reset clears both. */
+fbp_status fbp_profile_enable(fbp_plan_t plan, int enable);
+fbp_status fbp_profile_reset(fbp_plan_t plan);
+fbp_status fbp_profile_read(fbp_plan_t plan, int kernel, double* total_ms, long long* launches);
+
+/* Static text for a status code. */
+const char* fbp_status_str(fbp_status status);
+
+/* Synchronise the plan's device and read (then clear) the plan's device status word, set
+ * by kernels whose bounded waits or consistency checks failed.  FBP_OK if none. */
+fbp_status fbp_last_device_error(fbp_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FBP_H */

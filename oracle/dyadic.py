@@ -40,18 +40,21 @@ def _log2(N: int) -> int:
     return n
 
 
-def pattern_backproject(Lq) -> np.ndarray:
-    """Brute-force sums F[tau][u] = sum_i L[i][u + d_tau(i)] (float64), i ascending."""
+def pattern_backproject(Lq, taus=None) -> np.ndarray:
+    """Brute-force sums F[tau][u] = sum_i L[i][u + d_tau(i)] (float64), i ascending.
+
+    ``taus`` restricts the output to those slopes (rows of the result, in that order)."""
     Lq = np.asarray(Lq, dtype=np.float64)
     N, W = Lq.shape
     n = _log2(N)
     u = np.arange(N)
     rows = np.arange(N)
-    F = np.empty((N, N))
-    for tau in range(N):
+    taus = range(N) if taus is None else list(taus)
+    F = np.empty((len(taus), N))
+    for j, tau in enumerate(taus):
         cols = u[:, None] + dyadic_pattern(n, tau)[None, :]       # [u][i]
         vals = np.where(cols < W, Lq[rows[None, :], np.minimum(cols, W - 1)], 0.0)
-        F[tau] = vals.sum(axis=1)
+        F[j] = vals.sum(axis=1)
     return F
 
 

@@ -1,0 +1,280 @@
+"""Thin ctypes binding of libfbp (include/fbp.h): same names, argument marshalling only.
+
+Every step of the reconstruction runs in the library's CUDA kernels; this module checks
+shapes, dtypes and devices of torch tensors, passes their device pointers and the current
+CUDA stream, and turns status codes into exceptions.  There is no fallback: if the
+library is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfbp.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "fbp.h")
+MAX_ORDER = 8
+
+_STATUS = {0: "FBP_OK", 1: "FBP_ERR_INVALID_ARG", 2: "FBP_ERR_UNSUPPORTED",
+           3: "FBP_ERR_MISALIGNED", 4: "FBP_ERR_OOM", 5: "FBP_ERR_CUDA",
+           6: "FBP_ERR_TIMEOUT", 7: "FBP_ERR_INTERNAL"}
+
+
+class FbpError(RuntimeError):
+    def __init__(self, fn, code):
+        self.code = code
+        super().__init__(f"{fn} failed: {_STATUS.get(code, code)} ({fbp_status_str(code)})")
+
+
+class fbp_iir_coeffs(ctypes.Structure):
+    _fields_ = [("mb", ctypes.c_int), ("q", ctypes.c_int),
+                ("b", ctypes.c_double * MAX_ORDER), ("a", ctypes.c_double * MAX_ORDER)]
+
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libfbp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"libfbp.so not found at {path}; build it with "
+                          "paper_2007_06289_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, F, V, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
+    sig = {
+        "fbp_default_coeffs": (I, [I, I, ctypes.POINTER(fbp_iir_coeffs)]),
+        "fbp_plan": (I, [ctypes.POINTER(P), I, I, I, I, ctypes.POINTER(fbp_iir_coeffs), I]),
+        "fbp_plan_destroy": (I, [P]),
+        "fbp_workspace_bytes": (S, [P]),
+        "fbp_set_workspace": (I, [P, V, S]),
+        "fbp_filter_iir": (I, [P, V, V, V]),
+        "fbp_resample_st": (I, [P, V, V, V]),
+        "fbp_fht_backproject": (I, [P, V, V, V]),
+        "fbp_reconstruct": (I, [P, V, V, V]),
+        "fbp_reconstruct_host": (I, [P, V, V, I, V]),
+        "fbp_direct_reconstruct": (I, [P, V, V, V]),
+        "fbp_plan_info": (I, [P] + [ctypes.POINTER(I)] * 6),
+        "fbp_profile_enable": (I, [P, I]),
+        "fbp_profile_reset": (I, [P]),
+        "fbp_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_longlong)]),
+        "fbp_status_str": (ctypes.c_char_p, [I]),
+        "fbp_last_device_error": (I, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    del F
+    _lib = lib
+    return lib
+
+
+def header_functions(path: str = HEADER) -> list[str]:
+    """Names of the functions that include/fbp.h declares."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\*?\s+\**(fbp_\w+)\s*\(", text, flags=re.M)))
+
+
+def _check(fn, code):
+    if code != 0:
+        raise FbpError(fn, code)
+
+
+def fbp_status_str(code: int) -> str:
+    return load_library().fbp_status_str(int(code)).decode()
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dev_ptr(t, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor")
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous float32 CUDA tensor")
+    if t.numel() != _prod(shape):
+        raise ValueError(f"{name}: expected {shape} elements, got shape {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _prod(shape):
+    out = 1
+    for v in shape:
+        out *= v
+    return out
+
+
+def coeffs_struct(b, a) -> fbp_iir_coeffs:
+    c = fbp_iir_coeffs()
+    c.mb, c.q = len(b), len(a)
+    if not (1 <= c.mb <= MAX_ORDER and 0 <= c.q <= MAX_ORDER):
+        raise ValueError("filter order must be <= 8")
+    for k, v in enumerate(b):
+        c.b[k] = float(v)
+    for k, v in enumerate(a):
+        c.a[k] = float(v)
+    return c
+
+
+def fbp_default_coeffs(N: int, order: int = 0):
+    """(b, a) lists of the built-in fitted filter for image size N (float64)."""
+    c = fbp_iir_coeffs()
+    _check("fbp_default_coeffs", load_library().fbp_default_coeffs(N, order, ctypes.byref(c)))
+    return [c.b[k] for k in range(c.mb)], [c.a[k] for k in range(c.q)]
+
+
+class Plan:
+    """Owner of an fbp_plan_t handle (destroyed with the object)."""
+
+    def __init__(self, N, K, M, batch, coeffs=None, fuse_k=0):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        cs = None if coeffs is None else ctypes.byref(coeffs_struct(*coeffs))
+        _check("fbp_plan", lib.fbp_plan(ctypes.byref(h), N, K, M, batch, cs, fuse_k))
+        self._h = h
+        self.N, self.K, self.M, self.batch = N, K, M, batch
+        vals = [ctypes.c_int() for _ in range(6)]
+        _check("fbp_plan_info", lib.fbp_plan_info(h, *[ctypes.byref(v) for v in vals]))
+        self.fuse_k, self.chunk = vals[4].value, vals[5].value
+        self._ws = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().fbp_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # shapes
+    @property
+    def sino_shape(self):
+        return (self.batch, self.K, self.M)
+
+    @property
+    def lin_shape(self):
+        return (self.batch, 4, self.N, 2 * self.N)
+
+    @property
+    def img_shape(self):
+        return (self.batch, self.N, self.N)
+
+
+def fbp_plan(N: int, K: int, M: int, batch: int = 1, coeffs=None, fuse_k: int = 0) -> Plan:
+    return Plan(N, K, M, batch, coeffs, fuse_k)
+
+
+def fbp_plan_destroy(plan: Plan) -> None:
+    plan.close()
+
+
+def fbp_workspace_bytes(plan: Plan) -> int:
+    return int(load_library().fbp_workspace_bytes(plan.handle))
+
+
+def fbp_set_workspace(plan: Plan, ws) -> None:
+    """Give the plan a caller-owned workspace (a CUDA uint8 tensor kept alive by the plan)."""
+    lib = load_library()
+    if ws is None:
+        _check("fbp_set_workspace", lib.fbp_set_workspace(plan.handle, None, 0))
+    else:
+        _check("fbp_set_workspace",
+               lib.fbp_set_workspace(plan.handle, ctypes.c_void_p(ws.data_ptr()),
+                                     ws.numel() * ws.element_size()))
+    plan._ws = ws
+
+
+def fbp_plan_info(plan: Plan) -> dict:
+    return dict(N=plan.N, K=plan.K, M=plan.M, batch=plan.batch, fuse_k=plan.fuse_k,
+                chunk=plan.chunk)
+
+
+def fbp_filter_iir(plan: Plan, sino, filt, stream=None) -> None:
+    _check("fbp_filter_iir", load_library().fbp_filter_iir(
+        plan.handle, _dev_ptr(sino, plan.sino_shape, "sino"),
+        _dev_ptr(filt, plan.sino_shape, "filt"), _stream_ptr(stream)))
+
+
+def fbp_resample_st(plan: Plan, filt, lin, stream=None) -> None:
+    _check("fbp_resample_st", load_library().fbp_resample_st(
+        plan.handle, _dev_ptr(filt, plan.sino_shape, "filt"),
+        _dev_ptr(lin, plan.lin_shape, "lin"), _stream_ptr(stream)))
+
+
+def fbp_fht_backproject(plan: Plan, lin, img, stream=None) -> None:
+    _check("fbp_fht_backproject", load_library().fbp_fht_backproject(
+        plan.handle, _dev_ptr(lin, plan.lin_shape, "lin"),
+        _dev_ptr(img, plan.img_shape, "img"), _stream_ptr(stream)))
+
+
+def fbp_reconstruct(plan: Plan, sino, img, stream=None) -> None:
+    _check("fbp_reconstruct", load_library().fbp_reconstruct(
+        plan.handle, _dev_ptr(sino, plan.sino_shape, "sino"),
+        _dev_ptr(img, plan.img_shape, "img"), _stream_ptr(stream)))
+
+
+def fbp_direct_reconstruct(plan: Plan, sino, img, stream=None) -> None:
+    _check("fbp_direct_reconstruct", load_library().fbp_direct_reconstruct(
+        plan.handle, _dev_ptr(sino, plan.sino_shape, "sino"),
+        _dev_ptr(img, plan.img_shape, "img"), _stream_ptr(stream)))
+
+
+def fbp_reconstruct_host(plan: Plan, h_sino, h_img, count=None, stream=None) -> None:
+    """Host (preferably pinned) float32 CPU tensors [count][K][M] -> [count][N][N]."""
+    import torch
+    for t, nm in ((h_sino, "h_sino"), (h_img, "h_img")):
+        if not isinstance(t, torch.Tensor) or t.is_cuda or t.dtype != torch.float32 \
+                or not t.is_contiguous():
+            raise ValueError(f"{nm}: expected a contiguous float32 CPU tensor")
+    count = count if count is not None else h_sino.shape[0]
+    if h_sino.numel() < count * plan.K * plan.M or h_img.numel() < count * plan.N * plan.N:
+        raise ValueError("host buffers too small for count slices")
+    _check("fbp_reconstruct_host", load_library().fbp_reconstruct_host(
+        plan.handle, ctypes.c_void_p(h_sino.data_ptr()), ctypes.c_void_p(h_img.data_ptr()),
+        int(count), _stream_ptr(stream)))
+
+
+KERNELS = ("iir", "resample", "pass1_resample", "pass1_linogram", "pass2", "fir", "direct_bp")
+
+
+def fbp_profile_enable(plan: Plan, enable: bool = True) -> None:
+    _check("fbp_profile_enable", load_library().fbp_profile_enable(plan.handle, int(enable)))
+
+
+def fbp_profile_reset(plan: Plan) -> None:
+    _check("fbp_profile_reset", load_library().fbp_profile_reset(plan.handle))
+
+
+def fbp_profile_read(plan: Plan) -> dict:
+    """{kernel name: (event-timed ms, launches)} since the last reset."""
+    lib = load_library()
+    out = {}
+    for k, name in enumerate(KERNELS):
+        ms, n = ctypes.c_double(), ctypes.c_longlong()
+        _check("fbp_profile_read", lib.fbp_profile_read(plan.handle, k, ctypes.byref(ms),
+                                                        ctypes.byref(n)))
+        out[name] = (ms.value, n.value)
+    return out
+
+
+def fbp_last_device_error(plan: Plan) -> int:
+    return int(load_library().fbp_last_device_error(plan.handle))

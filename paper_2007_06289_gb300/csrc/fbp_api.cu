@@ -1,0 +1,746 @@
+// C ABI of libfbp: plans, geometry tables, workspace and the entry points of include/fbp.h.
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <complex>
+#include <new>
+#include <vector>
+
+#include "fbp_internal.h"
+
+namespace fbp {
+cudaError_t prepare_fht_kernels();
+cudaError_t prepare_iir_kernels();
+cudaError_t prepare_direct_kernels();
+}
+
+namespace {
+
+struct TableEntry {
+    int N;
+    int order;
+    double b[FBP_MAX_ORDER];
+    double a[FBP_MAX_ORDER];
+};
+
+const TableEntry kTable[] = {
+#include "iir_table.inc"
+};
+
+constexpr int kDefaultOrder = 3;
+constexpr size_t kAlign = 256;
+constexpr size_t kL2Budget = (size_t)96 << 20;   // bytes of filtered sinogram + G per chunk
+constexpr size_t kMaxChunk = 4096;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+fbp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FBP_OK : FBP_ERR_CUDA; }
+
+// Switches to the plan's device for the lifetime of the guard.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Stability by the step-down (Schur-Cohn) recursion: all reflection coefficients |k| < 1.
+bool stable(const double* a, int q)
+{
+    std::vector<double> c(a, a + q);
+    for (int m = q; m >= 1; --m) {
+        const double k = c[m - 1];
+        if (!(fabs(k) < 1.0)) return false;
+        std::vector<double> nc(m - 1);
+        for (int j = 0; j < m - 1; ++j) nc[j] = (c[j] - k * c[m - 2 - j]) / (1.0 - k * k);
+        c.swap(nc);
+    }
+    return true;
+}
+
+using cplx = std::complex<double>;
+
+// Roots of the monic z^q + a[0] z^(q-1) + ... + a[q-1] (Aberth-Ehrlich iteration, then
+// Newton polishing), q <= 8.
+std::vector<cplx> poly_roots(const double* a, int q)
+{
+    std::vector<cplx> z(q);
+    if (q == 0) return z;
+    auto eval = [&](cplx x, cplx& dp) {
+        cplx p = 1.0;
+        dp = 0.0;
+        for (int k = 0; k < q; ++k) {
+            dp = dp * x + p;
+            p = p * x + a[k];
+        }
+        return p;
+    };
+    double rad = 0.0;
+    for (int k = 0; k < q; ++k) rad = fmax(rad, pow(fabs(a[k]), 1.0 / (k + 1)));
+    rad = fmax(rad, 0.5);
+    for (int i = 0; i < q; ++i) z[i] = std::polar(rad, 2.0 * M_PI * i / q + 0.4);
+    for (int it = 0; it < 1000; ++it) {
+        double worst = 0.0;
+        for (int i = 0; i < q; ++i) {
+            cplx dp;
+            const cplx p = eval(z[i], dp);
+            if (p == 0.0) continue;
+            const cplx w = p / dp;
+            cplx s = 0.0;
+            for (int j = 0; j < q; ++j)
+                if (j != i) s += 1.0 / (z[i] - z[j]);
+            const cplx stepv = w / (1.0 - w * s);
+            z[i] -= stepv;
+            worst = fmax(worst, std::abs(stepv) / fmax(1.0, std::abs(z[i])));
+        }
+        if (worst < 1e-16) break;
+    }
+    for (int i = 0; i < q; ++i)
+        for (int it = 0; it < 3; ++it) {
+            cplx dp;
+            const cplx p = eval(z[i], dp);
+            if (std::abs(dp) > 0.0) z[i] -= p / dp;
+        }
+    return z;
+}
+
+// Parallel form of the causal filter B(w)/A(w), w = z^-1 (Eq. 9):
+//   B(w)/A(w) = D(w) + sum_j r_j / (1 - p_j w),  p_j the roots of z^q + a_1 z^(q-1) + ...,
+// D the polynomial part (present when mb > q).  Fills the kernel parameters and checks the
+// realisation against the direct-form impulse response in float64.
+fbp_status build_iir_params(fbp_plan_s* p)
+{
+    fbp::IirParams& prm = p->iir;
+    memset(&prm, 0, sizeof(prm));
+    int L = (p->M + 31) / 32;
+    if ((L & 1) == 0) ++L;                 // odd stride: conflict-free shared-memory lanes
+    prm.L = L;
+
+    int q = p->coeffs.q;
+    const int mb = p->coeffs.mb;
+    while (q > 0 && p->coeffs.a[q - 1] == 0.0) --q;       // trailing zero coefficients
+    const double* a = p->coeffs.a;
+    const double* b = p->coeffs.b;
+
+    // polynomial part and proper remainder (long division in powers of w)
+    std::vector<double> rem(b, b + mb), D;
+    if (mb - 1 >= q) {
+        if (q == 0) {
+            D = rem;
+            rem.assign(1, 0.0);
+        } else {
+            D.assign(mb - q, 0.0);
+            for (int deg = mb - 1; deg >= q; --deg) {
+                const double c = rem[deg] / a[q - 1];          // a_q is the w^q coefficient
+                D[deg - q] = c;
+                rem[deg - q] -= c;                             // w^0 coefficient of A is 1
+                for (int k = 1; k <= q; ++k) rem[deg - q + k] -= c * a[k - 1];
+            }
+            rem.resize(q);
+        }
+    }
+    if ((int)D.size() > fbp::kMaxOrder) return FBP_ERR_UNSUPPORTED;
+    prm.nd = (int)D.size();
+    for (int k = 0; k < prm.nd; ++k) prm.d[k] = (float)D[k];
+
+    const std::vector<cplx> pole = poly_roots(a, q);
+    for (int i = 0; i < q; ++i) {
+        if (!(std::abs(pole[i]) < 1.0)) return FBP_ERR_INVALID_ARG;     // unstable
+        for (int j = 0; j < i; ++j)
+            if (std::abs(pole[i] - pole[j]) < 1e-7) return FBP_ERR_UNSUPPORTED;   // repeated
+    }
+    auto Bp = [&](cplx w) {
+        cplx s = 0.0;
+        for (int k = (int)rem.size() - 1; k >= 0; --k) s = s * w + rem[k];
+        return s;
+    };
+    std::vector<cplx> res(q);
+    for (int j = 0; j < q; ++j) {
+        cplx den = 1.0;
+        for (int i = 0; i < q; ++i)
+            if (i != j) den *= 1.0 - pole[i] / pole[j];
+        res[j] = Bp(1.0 / pole[j]) / den;
+    }
+
+    // impulse-response check of the parallel form against the recursion in float64
+    {
+        const int T = 96;
+        std::vector<double> h(T, 0.0);
+        double scale = 0.0;
+        for (int n = 0; n < T; ++n) {
+            double v = n < mb ? b[n] : 0.0;
+            for (int k = 1; k <= q; ++k)
+                if (n - k >= 0) v -= a[k - 1] * h[n - k];
+            h[n] = v;
+            scale = fmax(scale, fabs(v));
+        }
+        double err = 0.0;
+        for (int n = 0; n < T; ++n) {
+            cplx g = n < prm.nd ? D[n] : 0.0;
+            for (int j = 0; j < q; ++j) g += res[j] * std::pow(pole[j], n);
+            err = fmax(err, fabs(g.real() - h[n]));
+        }
+        if (!(err <= 1e-9 * fmax(scale, 1e-300))) return FBP_ERR_UNSUPPORTED;
+    }
+
+    // real modes, and one representative (Im p > 0) per conjugate pair with doubled residue
+    for (int j = 0; j < q; ++j) {
+        const cplx pj = pole[j];
+        const bool real = fabs(pj.imag()) <= 1e-12 * fmax(1.0, std::abs(pj));
+        cplx carry = std::pow(pj, L);
+        if (real) {
+            const int m = prm.jr++;
+            prm.rp[m] = (float)pj.real();
+            prm.rr[m] = (float)res[j].real();
+            double c = carry.real();
+            for (int d = 0; d < fbp::kScanSteps; ++d, c *= c) prm.rpow[d][m] = (float)c;
+        } else if (pj.imag() > 0.0) {
+            const int m = prm.jc++;
+            prm.cpr[m] = (float)pj.real();
+            prm.cpi[m] = (float)pj.imag();
+            prm.crr[m] = (float)(2.0 * res[j].real());
+            prm.cri[m] = (float)(2.0 * res[j].imag());
+            for (int d = 0; d < fbp::kScanSteps; ++d, carry *= carry) {
+                prm.cpowr[d][m] = (float)carry.real();
+                prm.cpowi[d][m] = (float)carry.imag();
+            }
+        }
+    }
+    if (prm.jr + 2 * prm.jc != q) return FBP_ERR_UNSUPPORTED;     // unpaired complex root
+    return FBP_OK;
+}
+
+void split(double v, float& hi, float& lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+// Per (quarter, row) sampling geometry, computed in float64 (Sec. 4.1-4.2, Eq. 14-15).
+// Quarter order v-, v+, h-, h+; row i has slope sigma = i/(N-1).  Normal angle theta:
+// atan(sigma), pi - atan(sigma), pi/2 - atan(sigma), pi/2 + atan(sigma).  For stored
+// column c (intercept u = c, or N-1-c for the '+' quarters) the signed offset from the
+// centre c0 is r = (c - c0 (1 + sigma)) / sqrt(1 + sigma^2), negated for h+.
+std::vector<fbp::RowGeom> build_geometry(int N, int K, int M)
+{
+    std::vector<fbp::RowGeom> g(4 * (size_t)N);
+    const double c0 = 0.5 * (N - 1);
+    const double half = 0.5 * (M - 1);
+    for (int q = 0; q < 4; ++q) {
+        for (int i = 0; i < N; ++i) {
+            const double s = (double)i / (N - 1);
+            const double at = atan(s);
+            double theta;
+            switch (q) {
+                case 0: theta = at; break;
+                case 1: theta = M_PI - at; break;
+                case 2: theta = 0.5 * M_PI - at; break;
+                default: theta = 0.5 * M_PI + at; break;
+            }
+            double tk = theta * K / M_PI;
+            double k0 = floor(tk);
+            if (k0 > K - 1) k0 = K - 1;
+            fbp::RowGeom& e = g[(size_t)q * N + i];
+            e.k0 = (int)k0;
+            e.ft = (float)(tk - k0);
+            e.wrap = (e.k0 + 1 >= K) ? 1 : 0;
+            double w = (1.0 / (N - 1)) / (1.0 + s * s);
+            if (i == 0 || i == N - 1) w *= 0.5;
+            e.w = (float)w;
+            const double inv = 1.0 / sqrt(1.0 + s * s);
+            double A = inv, B = -c0 * (1.0 + s) * inv;
+            if (q == 3) { A = -A; B = -B; }
+            split(A, e.a_hi, e.a_lo);
+            split(B + half, e.b_hi, e.b_lo);
+        }
+    }
+    return g;
+}
+
+int ilog2(int v)
+{
+    int n = 0;
+    while ((1 << n) < v) ++n;
+    return n;
+}
+
+fbp_status ensure_workspace(fbp_plan_s* p)
+{
+    if (p->ws) return FBP_OK;
+    void* ws = nullptr;
+    if (cudaMalloc(&ws, p->ws_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return FBP_ERR_OOM;
+    }
+    p->ws = ws;
+    p->ws_owned = 1;
+    return FBP_OK;
+}
+
+float* ws_ptr(const fbp_plan_s* p, size_t off) { return (float*)((char*)p->ws + off); }
+
+cudaEvent_t prof_event(fbp_plan_s* p)
+{
+    if (!p->prof_pool.empty()) {
+        cudaEvent_t e = p->prof_pool.back();
+        p->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Issues one kernel launch `f` on stream st, counting it and, with profiling on, bracketing
+// it with CUDA events on the same stream.
+template <class F>
+cudaError_t run(fbp_plan_s* p, int kernel, cudaStream_t st, F&& f)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (p->prof_on) {
+        a = prof_event(p);
+        b = prof_event(p);
+        if (a && b) cudaEventRecord(a, st);
+    }
+    const cudaError_t e = f();
+    if (a && b) {
+        cudaEventRecord(b, st);
+        p->prof_pending.push_back({kernel, a, b});
+    } else {
+        if (a) p->prof_pool.push_back(a);
+        if (b) p->prof_pool.push_back(b);
+    }
+    if (e == cudaSuccess) ++p->launches[kernel];
+    return e;
+}
+
+// Folds finished event pairs into the per-kernel totals.
+cudaError_t prof_collect(fbp_plan_s* p)
+{
+    cudaError_t err = cudaSuccess;
+    for (const fbp_plan_s::Timed& t : p->prof_pending) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(t.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t.a, t.b);
+        if (e == cudaSuccess) p->prof_ms[t.kernel] += ms;
+        else err = e;
+        p->prof_pool.push_back(t.a);
+        p->prof_pool.push_back(t.b);
+    }
+    p->prof_pending.clear();
+    return err;
+}
+
+// One chunk of the fused pipeline: filter -> (resample + pass 1) -> (pass 2 + sum).
+cudaError_t reconstruct_chunk(fbp_plan_s* p, const float* sino, float* img, int cnt,
+                              cudaStream_t st)
+{
+    float* filt = ws_ptr(p, p->off_filt);
+    float* g = ws_ptr(p, p->off_g);
+    cudaError_t e = run(p, FBP_KERNEL_IIR, st,
+                        [&] { return fbp::launch_iir(p, sino, filt, cnt * p->K, st); });
+    if (e == cudaSuccess)
+        e = run(p, FBP_KERNEL_PASS1_RESAMPLE, st,
+                [&] { return fbp::launch_pass1(p, filt, false, g, cnt, st); });
+    if (e == cudaSuccess)
+        e = run(p, FBP_KERNEL_PASS2, st, [&] { return fbp::launch_pass2(p, g, img, cnt, st); });
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fbp_status_str(fbp_status s)
+{
+    switch (s) {
+        case FBP_OK: return "ok";
+        case FBP_ERR_INVALID_ARG: return "invalid argument";
+        case FBP_ERR_UNSUPPORTED: return "unsupported size or order";
+        case FBP_ERR_MISALIGNED: return "pointer not 16-byte aligned";
+        case FBP_ERR_OOM: return "out of memory";
+        case FBP_ERR_CUDA: return "CUDA error";
+        case FBP_ERR_TIMEOUT: return "bounded wait timed out";
+        case FBP_ERR_INTERNAL: return "internal consistency check failed";
+    }
+    return "unknown status";
+}
+
+fbp_status fbp_default_coeffs(int N, int order, fbp_iir_coeffs* out)
+{
+    if (!out) return FBP_ERR_INVALID_ARG;
+    if (order <= 0) order = kDefaultOrder;
+    for (const TableEntry& t : kTable) {
+        if (t.N == N && t.order == order) {
+            memset(out, 0, sizeof(*out));
+            out->mb = order;
+            out->q = order;
+            for (int k = 0; k < order; ++k) {
+                out->b[k] = t.b[k];
+                out->a[k] = t.a[k];
+            }
+            return FBP_OK;
+        }
+    }
+    return FBP_ERR_UNSUPPORTED;
+}
+
+fbp_status fbp_plan(fbp_plan_t* out, int N, int K, int M, int batch,
+                    const fbp_iir_coeffs* coeffs, int fuse_k)
+{
+    if (!out) return FBP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (N < 2 || N > 4096 || (N & (N - 1)) != 0) return FBP_ERR_UNSUPPORTED;
+    if (K < 2 || M < 2 || M > 28000 || batch < 1) return FBP_ERR_INVALID_ARG;
+    fbp_iir_coeffs c;
+    if (coeffs) {
+        c = *coeffs;
+    } else {
+        fbp_status st = fbp_default_coeffs(N, 0, &c);
+        if (st != FBP_OK) return st;
+    }
+    if (c.mb < 1 || c.mb > FBP_MAX_ORDER || c.q < 0 || c.q > FBP_MAX_ORDER)
+        return FBP_ERR_UNSUPPORTED;
+    double ad[FBP_MAX_ORDER];
+    for (int k = 0; k < c.mb; ++k)
+        if (!isfinite(c.b[k])) return FBP_ERR_INVALID_ARG;
+    for (int k = 0; k < c.q; ++k) {
+        if (!isfinite(c.a[k])) return FBP_ERR_INVALID_ARG;
+        ad[k] = c.a[k];
+    }
+    if (!stable(ad, c.q)) return FBP_ERR_INVALID_ARG;
+
+    const int n = ilog2(N);
+    int n1, n2;
+    if (fuse_k == 0) {
+        n1 = n <= 6 ? n : (n + 1) / 2;
+    } else {
+        if (fuse_k < 1 || fuse_k > 6) return FBP_ERR_UNSUPPORTED;
+        n1 = fuse_k < n ? fuse_k : n;
+    }
+    n2 = n - n1;
+    if (n2 > 6) return FBP_ERR_UNSUPPORTED;
+
+    fbp_plan_s* p = new (std::nothrow) fbp_plan_s();
+    if (!p) return FBP_ERR_OOM;
+    p->N = N; p->K = K; p->M = M; p->batch = batch;
+    p->n = n; p->n1 = n1; p->n2 = n2;
+    p->coeffs = c;
+    {
+        const fbp_status fs = build_iir_params(p);
+        if (fs != FBP_OK) { delete p; return fs; }
+    }
+    if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return FBP_ERR_CUDA; }
+
+    const size_t s_bytes = fbp::sino_floats(p) * sizeof(float);
+    const size_t g_bytes = fbp::lin_floats(p) * sizeof(float);
+    size_t chunk = kL2Budget / (s_bytes + g_bytes);
+    if (chunk < 1) chunk = 1;
+    if (chunk > kMaxChunk) chunk = kMaxChunk;          // grid.z limit of the per-slice kernels
+    if (chunk > (size_t)batch) chunk = batch;
+    p->chunk = (int)chunk;
+    size_t off = 0;
+    p->off_filt = off; off = align_up(off + chunk * s_bytes);
+    p->off_g = off; off = align_up(off + chunk * g_bytes);
+    for (int b = 0; b < 2; ++b) { p->off_stage_sino[b] = off; off = align_up(off + chunk * s_bytes); }
+    for (int b = 0; b < 2; ++b) {
+        p->off_stage_img[b] = off;
+        off = align_up(off + chunk * fbp::img_floats(p) * sizeof(float));
+    }
+    p->ws_bytes = off;
+
+    fbp_status st = FBP_OK;
+    std::vector<fbp::RowGeom> geo = build_geometry(N, K, M);
+    std::vector<float2> trig(K);
+    for (int k = 0; k < K; ++k) {
+        const double th = k * M_PI / K;
+        trig[k] = make_float2((float)cos(th), (float)sin(th));
+    }
+    cudaError_t e = cudaMalloc(&p->d_geom, geo.size() * sizeof(fbp::RowGeom));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_trig, trig.size() * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
+    if (e != cudaSuccess) st = FBP_ERR_OOM;
+    if (st == FBP_OK) {
+        e = cudaMemcpy(p->d_geom, geo.data(), geo.size() * sizeof(fbp::RowGeom), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p->d_trig, trig.data(), trig.size() * sizeof(float2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+        if (e == cudaSuccess) e = fbp::prepare_fht_kernels();
+        if (e == cudaSuccess) e = fbp::prepare_iir_kernels();
+        if (e == cudaSuccess) e = fbp::prepare_direct_kernels();
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->st_h2d, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->st_comp, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->st_d2h, cudaStreamNonBlocking);
+        const unsigned ef = cudaEventDisableTiming;
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, ef);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_done, ef);
+        for (int b = 0; b < 2; ++b) {
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_h2d[b], ef);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_comp[b], ef);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_free[b], ef);
+        }
+        if (e != cudaSuccess) st = FBP_ERR_CUDA;
+    }
+    if (st != FBP_OK) {
+        cudaGetLastError();
+        fbp_plan_destroy(p);
+        return st;
+    }
+    *out = p;
+    return FBP_OK;
+}
+
+fbp_status fbp_plan_destroy(fbp_plan_t p)
+{
+    if (!p) return FBP_OK;
+    DeviceGuard g(p->device);
+    cudaDeviceSynchronize();
+    if (p->ws_owned && p->ws) cudaFree(p->ws);
+    if (p->d_geom) cudaFree(p->d_geom);
+    if (p->d_trig) cudaFree(p->d_trig);
+    if (p->d_status) cudaFree(p->d_status);
+    cudaStream_t ss[3] = {p->st_h2d, p->st_comp, p->st_d2h};
+    for (cudaStream_t s : ss)
+        if (s) cudaStreamDestroy(s);
+    cudaEvent_t es[2] = {p->ev_start, p->ev_done};
+    for (cudaEvent_t ev : es)
+        if (ev) cudaEventDestroy(ev);
+    for (const fbp_plan_s::Timed& t : p->prof_pending) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    for (cudaEvent_t ev : p->prof_pool) cudaEventDestroy(ev);
+    for (int b = 0; b < 2; ++b) {
+        if (p->ev_h2d[b]) cudaEventDestroy(p->ev_h2d[b]);
+        if (p->ev_comp[b]) cudaEventDestroy(p->ev_comp[b]);
+        if (p->ev_free[b]) cudaEventDestroy(p->ev_free[b]);
+    }
+    cudaGetLastError();
+    delete p;
+    return FBP_OK;
+}
+
+size_t fbp_workspace_bytes(fbp_plan_t p) { return p ? p->ws_bytes : 0; }
+
+fbp_status fbp_set_workspace(fbp_plan_t p, void* d_ws, size_t bytes)
+{
+    if (!p) return FBP_ERR_INVALID_ARG;
+    if (d_ws && bytes < p->ws_bytes) return FBP_ERR_INVALID_ARG;
+    if (d_ws && !aligned16(d_ws)) return FBP_ERR_MISALIGNED;
+    if (p->ws_owned && p->ws) {
+        DeviceGuard g(p->device);
+        cudaDeviceSynchronize();
+        cudaFree(p->ws);
+    }
+    p->ws = d_ws;
+    p->ws_owned = 0;
+    return FBP_OK;
+}
+
+fbp_status fbp_plan_info(fbp_plan_t p, int* N, int* K, int* M, int* batch, int* fuse_k,
+                         int* chunk)
+{
+    if (!p) return FBP_ERR_INVALID_ARG;
+    if (N) *N = p->N;
+    if (K) *K = p->K;
+    if (M) *M = p->M;
+    if (batch) *batch = p->batch;
+    if (fuse_k) *fuse_k = p->n1;
+    if (chunk) *chunk = p->chunk;
+    return FBP_OK;
+}
+
+fbp_status fbp_filter_iir(fbp_plan_t p, const float* d_sino, float* d_filt, void* stream)
+{
+    if (!p || !d_sino || !d_filt) return FBP_ERR_INVALID_ARG;
+    if (!aligned16(d_sino) || !aligned16(d_filt)) return FBP_ERR_MISALIGNED;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    return cuda_status(run(p, FBP_KERNEL_IIR, st, [&] {
+        return fbp::launch_iir(p, d_sino, d_filt, p->batch * p->K, st);
+    }));
+}
+
+fbp_status fbp_resample_st(fbp_plan_t p, const float* d_filt, float* d_lin, void* stream)
+{
+    if (!p || !d_filt || !d_lin) return FBP_ERR_INVALID_ARG;
+    if (!aligned16(d_filt) || !aligned16(d_lin)) return FBP_ERR_MISALIGNED;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    for (int c = 0; c < p->batch; c += p->chunk) {
+        const int cnt = p->batch - c < p->chunk ? p->batch - c : p->chunk;
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaError_t e = run(p, FBP_KERNEL_RESAMPLE, st, [&] {
+            return fbp::launch_resample(p, d_filt + (size_t)c * fbp::sino_floats(p),
+                                        d_lin + (size_t)c * fbp::lin_floats(p), cnt, st);
+        });
+        if (e != cudaSuccess) return FBP_ERR_CUDA;
+    }
+    return FBP_OK;
+}
+
+fbp_status fbp_fht_backproject(fbp_plan_t p, const float* d_lin, float* d_img, void* stream)
+{
+    if (!p || !d_lin || !d_img) return FBP_ERR_INVALID_ARG;
+    if (!aligned16(d_lin) || !aligned16(d_img)) return FBP_ERR_MISALIGNED;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    fbp_status s = ensure_workspace(p);
+    if (s != FBP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    float* gbuf = ws_ptr(p, p->off_g);
+    for (int c = 0; c < p->batch; c += p->chunk) {
+        const int cnt = p->batch - c < p->chunk ? p->batch - c : p->chunk;
+        cudaError_t e = run(p, FBP_KERNEL_PASS1_LINOGRAM, st, [&] {
+            return fbp::launch_pass1(p, d_lin + (size_t)c * fbp::lin_floats(p), true, gbuf, cnt, st);
+        });
+        if (e == cudaSuccess)
+            e = run(p, FBP_KERNEL_PASS2, st, [&] {
+                return fbp::launch_pass2(p, gbuf, d_img + (size_t)c * fbp::img_floats(p), cnt, st);
+            });
+        if (e != cudaSuccess) return FBP_ERR_CUDA;
+    }
+    return FBP_OK;
+}
+
+fbp_status fbp_reconstruct(fbp_plan_t p, const float* d_sino, float* d_img, void* stream)
+{
+    if (!p || !d_sino || !d_img) return FBP_ERR_INVALID_ARG;
+    if (!aligned16(d_sino) || !aligned16(d_img)) return FBP_ERR_MISALIGNED;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    fbp_status s = ensure_workspace(p);
+    if (s != FBP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int c = 0; c < p->batch; c += p->chunk) {
+        const int cnt = p->batch - c < p->chunk ? p->batch - c : p->chunk;
+        cudaError_t e = reconstruct_chunk(p, d_sino + (size_t)c * fbp::sino_floats(p),
+                                          d_img + (size_t)c * fbp::img_floats(p), cnt, st);
+        if (e != cudaSuccess) return FBP_ERR_CUDA;
+    }
+    return FBP_OK;
+}
+
+fbp_status fbp_reconstruct_host(fbp_plan_t p, const float* h_sino, float* h_img, int count,
+                                void* stream)
+{
+    if (!p || !h_sino || !h_img || count < 1) return FBP_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    fbp_status s = ensure_workspace(p);
+    if (s != FBP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t sf = fbp::sino_floats(p), imf = fbp::img_floats(p);
+    cudaError_t e = cudaEventRecord(p->ev_start, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->st_h2d, p->ev_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->st_comp, p->ev_start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->st_d2h, p->ev_start, 0);
+    int ci = 0;
+    for (int c = 0; c < count && e == cudaSuccess; c += p->chunk, ++ci) {
+        const int b = ci & 1;
+        const int cnt = count - c < p->chunk ? count - c : p->chunk;
+        float* dsino = ws_ptr(p, p->off_stage_sino[b]);
+        float* dimg = ws_ptr(p, p->off_stage_img[b]);
+        if (ci >= 2) e = cudaStreamWaitEvent(p->st_h2d, p->ev_comp[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dsino, h_sino + (size_t)c * sf, (size_t)cnt * sf * sizeof(float),
+                                cudaMemcpyHostToDevice, p->st_h2d);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_h2d[b], p->st_h2d);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->st_comp, p->ev_h2d[b], 0);
+        if (e == cudaSuccess && ci >= 2) e = cudaStreamWaitEvent(p->st_comp, p->ev_free[b], 0);
+        if (e == cudaSuccess) e = reconstruct_chunk(p, dsino, dimg, cnt, p->st_comp);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_comp[b], p->st_comp);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->st_d2h, p->ev_comp[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_img + (size_t)c * imf, dimg, (size_t)cnt * imf * sizeof(float),
+                                cudaMemcpyDeviceToHost, p->st_d2h);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_free[b], p->st_d2h);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_done, p->st_d2h);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_done, 0);
+    return cuda_status(e);
+}
+
+fbp_status fbp_direct_reconstruct(fbp_plan_t p, const float* d_sino, float* d_img, void* stream)
+{
+    if (!p || !d_sino || !d_img) return FBP_ERR_INVALID_ARG;
+    if (!aligned16(d_sino) || !aligned16(d_img)) return FBP_ERR_MISALIGNED;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    fbp_status s = ensure_workspace(p);
+    if (s != FBP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    float* filt = ws_ptr(p, p->off_filt);
+    for (int c = 0; c < p->batch; c += p->chunk) {
+        const int cnt = p->batch - c < p->chunk ? p->batch - c : p->chunk;
+        cudaError_t e = run(p, FBP_KERNEL_FIR, st, [&] {
+            return fbp::launch_fir(p, d_sino + (size_t)c * fbp::sino_floats(p), filt, cnt * p->K, st);
+        });
+        if (e == cudaSuccess)
+            e = run(p, FBP_KERNEL_DIRECT_BP, st, [&] {
+                return fbp::launch_direct_bp(p, filt, d_img + (size_t)c * fbp::img_floats(p), cnt, st);
+            });
+        if (e != cudaSuccess) return FBP_ERR_CUDA;
+    }
+    return FBP_OK;
+}
+
+fbp_status fbp_profile_enable(fbp_plan_t p, int enable)
+{
+    if (!p) return FBP_ERR_INVALID_ARG;
+    p->prof_on = enable ? 1 : 0;
+    return FBP_OK;
+}
+
+fbp_status fbp_profile_reset(fbp_plan_t p)
+{
+    if (!p) return FBP_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    const cudaError_t e = prof_collect(p);
+    for (int k = 0; k < FBP_KERNEL_COUNT; ++k) {
+        p->prof_ms[k] = 0.0;
+        p->launches[k] = 0;
+    }
+    return cuda_status(e);
+}
+
+fbp_status fbp_profile_read(fbp_plan_t p, int kernel, double* total_ms, long long* launches)
+{
+    if (!p || kernel < 0 || kernel >= FBP_KERNEL_COUNT) return FBP_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    const cudaError_t e = prof_collect(p);
+    if (total_ms) *total_ms = p->prof_ms[kernel];
+    if (launches) *launches = p->launches[kernel];
+    return cuda_status(e);
+}
+
+fbp_status fbp_last_device_error(fbp_plan_t p)
+{
+    if (!p) return FBP_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return FBP_ERR_CUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FBP_ERR_CUDA;
+    if (v != 0 && cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return FBP_ERR_CUDA;
+    return (fbp_status)v;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Internal declarations shared by the translation units of libfbp (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/fbp.h"
+
+namespace fbp {
+
+constexpr int kMaxOrder = FBP_MAX_ORDER;
+constexpr int kScanSteps = 5;            // log2(32 lanes)
+
+// Per linogram row (quarter q, slope row i): where the row samples the filtered sinogram.
+// Detector index m(c) = A*c + B for stored column c, carried as float pairs (hi + lo) so
+// that the fractional position keeps ~2^-24 absolute accuracy at |m| ~ 4096.
+// Angle index k0 + ft; the second angle row is k0+1, or row 0 with the detector mirrored
+// (m -> M-1-m) when k0+1 == K ("wrap", p(theta+pi, r) = p(theta, -r)).
+struct RowGeom {
+    int k0;
+    int wrap;
+    float ft;
+    float w;        // row weight (trapezoid in sigma, Jacobian 1/k_t^2)
+    float a_hi, a_lo;
+    float b_hi, b_lo;
+};
+
+// The recursive filter in parallel (modal) form, as the kernel consumes it:
+//   g(n) = sum_j Re(r_j p_j^n) + d_n,   i.e.   y(n) = sum_j Re(r_j s_j(n)) + sum_k d_k x(n-k),
+//   s_j(n) = p_j s_j(n-1) + x(n).
+// jr real modes, jc complex modes (one per conjugate pair, residue doubled), nd direct taps.
+// pow*[d] = p^(L 2^d) carries a mode's state across 2^d lanes of L samples each.
+struct IirParams {
+    int jr, jc, nd, L;
+    float rp[kMaxOrder], rr[kMaxOrder];
+    float cpr[kMaxOrder / 2], cpi[kMaxOrder / 2], crr[kMaxOrder / 2], cri[kMaxOrder / 2];
+    float rpow[kScanSteps][kMaxOrder];
+    float cpowr[kScanSteps][kMaxOrder / 2], cpowi[kScanSteps][kMaxOrder / 2];
+    float d[kMaxOrder];
+};
+
+}  // namespace fbp
+
+struct fbp_plan_s {
+    int N, K, M, batch;
+    int n, n1, n2;          // log2 N, Hough stages in pass 1 and pass 2
+    int chunk;              // slices processed per kernel sequence
+    int device;
+    fbp_iir_coeffs coeffs;
+    fbp::IirParams iir;
+    fbp::RowGeom* d_geom;   // [4][N]
+    float2* d_trig;         // [K] (cos, sin) for the direct comparator
+    int* d_status;          // device status word
+    // workspace
+    void* ws;
+    size_t ws_bytes;
+    int ws_owned;
+    size_t off_filt, off_g, off_stage_sino[2], off_stage_img[2];
+    // host-API pipeline
+    cudaStream_t st_h2d, st_comp, st_d2h;
+    cudaEvent_t ev_start, ev_h2d[2], ev_comp[2], ev_free[2], ev_done;
+    // measurement hooks
+    long long launches[FBP_KERNEL_COUNT];
+    int prof_on;
+    struct Timed { int kernel; cudaEvent_t a, b; };
+    std::vector<Timed> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[FBP_KERNEL_COUNT];
+};
+
+namespace fbp {
+
+// Kernel launchers (each returns cudaGetLastError() after the launch).
+cudaError_t launch_iir(const fbp_plan_s* p, const float* in, float* out, int rows,
+                       cudaStream_t st);
+cudaError_t launch_resample(const fbp_plan_s* p, const float* filt, float* lin, int count,
+                            cudaStream_t st);
+cudaError_t launch_pass1(const fbp_plan_s* p, const float* src, bool from_lin, float* g,
+                         int count, cudaStream_t st);
+cudaError_t launch_pass2(const fbp_plan_s* p, const float* g, float* img, int count,
+                         cudaStream_t st);
+cudaError_t launch_fir(const fbp_plan_s* p, const float* in, float* out, int rows,
+                       cudaStream_t st);
+cudaError_t launch_direct_bp(const fbp_plan_s* p, const float* filt, float* img, int count,
+                             cudaStream_t st);
+
+inline size_t lin_floats(const fbp_plan_s* p) { return (size_t)4 * p->N * 2 * p->N; }
+inline size_t sino_floats(const fbp_plan_s* p) { return (size_t)p->K * p->M; }
+inline size_t img_floats(const fbp_plan_s* p) { return (size_t)p->N * p->N; }
+
+}  // namespace fbp

@@ -17,3 +17,12 @@ def pytest_configure(config):
 def coeff_table():
     from paper_2007_06289_gb300 import iir_fit
     return iir_fit.load_table()
+
+
+@pytest.fixture(scope="session")
+def fbp():
+    """The built library's Python binding (builds libfbp.so in-tree if it is stale)."""
+    from paper_2007_06289_gb300 import binding, build
+    build.build()
+    binding.load_library()
+    return binding

@@ -1,0 +1,61 @@
+"""The C ABI without a GPU: the library loads, exports every function include/fbp.h
+declares, and validates arguments on the host before touching CUDA."""
+import ctypes
+
+import numpy as np
+import pytest
+
+
+def test_every_declared_symbol_is_exported(fbp):
+    names = fbp.header_functions()
+    assert len(names) >= 14
+    lib = fbp.load_library()
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(fbp):
+    assert fbp.fbp_status_str(0) == "ok"
+    assert "aligned" in fbp.fbp_status_str(3)
+    assert fbp.fbp_status_str(99) == "unknown status"
+
+
+def test_default_coefficients_come_from_the_committed_table(fbp, coeff_table):
+    for e in coeff_table["entries"]:
+        b, a = fbp.fbp_default_coeffs(e["N"], e["order"])
+        np.testing.assert_array_equal(b, e["b"])
+        np.testing.assert_array_equal(a, e["a"])
+    b3, a3 = fbp.fbp_default_coeffs(256)
+    assert len(b3) == 3 and len(a3) == 3
+    with pytest.raises(fbp.FbpError):
+        fbp.fbp_default_coeffs(3, 3)
+
+
+def _plan_status(fbp, N, K, M, batch, coeffs, fuse_k=0):
+    lib = fbp.load_library()
+    h = ctypes.c_void_p()
+    cs = None if coeffs is None else ctypes.byref(fbp.coeffs_struct(*coeffs))
+    return lib.fbp_plan(ctypes.byref(h), N, K, M, batch, cs, fuse_k)
+
+
+def test_plan_rejects_bad_arguments_before_cuda(fbp):
+    good = ([0.12, -0.23, 0.11], list(np.poly([0.9, 0.5, -0.3])[1:]))
+    assert _plan_status(fbp, 96, 8, 8, 1, good) == 2            # N not a power of two
+    assert _plan_status(fbp, 8192, 8, 8, 1, good) == 2          # N too large
+    assert _plan_status(fbp, 64, 1, 8, 1, good) == 1            # K < 2
+    assert _plan_status(fbp, 64, 8, 8, 0, good) == 1            # batch < 1
+    assert _plan_status(fbp, 64, 8, 8, 1, ([1.0], [-1.01])) == 1    # pole at 1.01
+    repeated = ([0.1, -0.1, 0.0], list(np.poly([0.5, 0.5, 0.2])[1:]))
+    assert _plan_status(fbp, 64, 8, 8, 1, repeated) == 2        # repeated pole
+    assert _plan_status(fbp, 64, 8, 8, 1, good, fuse_k=7) == 2  # fuse_k out of range
+    assert _plan_status(fbp, 4096, 8, 8, 1, good, fuse_k=5) == 2   # second pass > 6 stages
+
+
+def test_null_pointers_are_rejected(fbp):
+    lib = fbp.load_library()
+    assert lib.fbp_plan(None, 64, 8, 8, 1, None, 0) == 1
+    assert lib.fbp_reconstruct(None, None, None, None) == 1
+    assert lib.fbp_filter_iir(None, None, None, None) == 1
+    assert lib.fbp_workspace_bytes(None) == 0
+    assert lib.fbp_plan_destroy(None) == 0
+    assert lib.fbp_default_coeffs(256, 3, None) == 1
