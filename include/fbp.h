@@ -127,6 +127,25 @@ fbp_status fbp_reconstruct(fbp_plan_t plan, const float* d_sino, float* d_img, v
 fbp_status fbp_reconstruct_host(fbp_plan_t plan, const float* h_sino, float* h_img, int count,
                                 void* stream);
 
+/* Allocation-free variant of fbp_fht_backproject, for callers that cannot allocate device
+ * memory (code running inside another framework's memory pool, plugins handed only their
+ * input and output buffers, real-time loops where an allocation may stall or fail): it
+ * needs no plan and no workspace.  The paper has no counterpart; this is an interface
+ * convenience.  d_lin [count][4][N][2N] (read only) -> d_img [count][N][N], same layout
+ * and bit-identical results as fbp_fht_backproject.
+ * Its scratch is a fixed device array inside the library, sized for one slice of N up to
+ * FBP_STATIC_MAX_N (8 MiB), which every GPU that loads the library holds until the process
+ * exits; slices are processed one after another through it.  No call allocates or frees
+ * memory.  The first call on a device looks up the array's device address and sets the
+ * kernels' shared-memory limits for that device, so make it before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race (issue them on one stream
+ * or order them with events).
+ * Errors: FBP_ERR_UNSUPPORTED (N not a power of two in [2, FBP_STATIC_MAX_N]),
+ * FBP_ERR_INVALID_ARG (count < 1, null pointer), FBP_ERR_MISALIGNED, FBP_ERR_CUDA. */
+#define FBP_STATIC_MAX_N 512
+fbp_status fbp_fht_backproject_static(int N, int count, const float* d_lin, float* d_img,
+                                      void* stream);
+
 /* Comparator, not the paper's method: direct Theta(N^3) FBP (Eq. 3-5 with the exact FIR
  * ramp of Eq. 8, L0 = M-1, and pixel-driven linear-interpolation back projection,
  * f = (pi/K) sum_k p~_k((x-c0) cos theta_k + (y-c0) sin theta_k)).

@@ -58,6 +58,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "fbp_reconstruct": (I, [P, V, V, V]),
         "fbp_reconstruct_host": (I, [P, V, V, I, V]),
         "fbp_direct_reconstruct": (I, [P, V, V, V]),
+        "fbp_fht_backproject_static": (I, [I, I, V, V, V]),
         "fbp_plan_info": (I, [P] + [ctypes.POINTER(I)] * 6),
         "fbp_profile_enable": (I, [P, I]),
         "fbp_profile_reset": (I, [P]),
@@ -224,6 +225,15 @@ def fbp_fht_backproject(plan: Plan, lin, img, stream=None) -> None:
     _check("fbp_fht_backproject", load_library().fbp_fht_backproject(
         plan.handle, _dev_ptr(lin, plan.lin_shape, "lin"),
         _dev_ptr(img, plan.img_shape, "img"), _stream_ptr(stream)))
+
+
+def fbp_fht_backproject_static(N: int, lin, img, stream=None) -> None:
+    """Hough back projection without a plan or workspace, for callers that cannot
+    allocate device memory (scratch is a fixed array inside the library, N <= 512)."""
+    count = lin.shape[0]
+    _check("fbp_fht_backproject_static", load_library().fbp_fht_backproject_static(
+        N, count, _dev_ptr(lin, (count, 4, N, 2 * N), "lin"),
+        _dev_ptr(img, (count, N, N), "img"), _stream_ptr(stream)))
 
 
 def fbp_reconstruct(plan: Plan, sino, img, stream=None) -> None:
