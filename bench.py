@@ -105,7 +105,8 @@ def byte_model(N: int, K: int, M: int, n1: int) -> dict:
     P = math.ceil(math.log2(N) / 6)
     G = 4 * 4 * g_needed_floats(N, n1)
     return dict(S=S, Lin=Lin, Img=Img, P=P, B_model=3 * S + (2 * P + 1) * Lin + Img,
-                compulsory=S + Img, iir=2 * S, pass1_resample=S + G, pass2=G + Img, G=G)
+                compulsory=S + Img, iir=2 * S, pass1_resample=S + G, pass2=G // 2 + Img,
+                pass2_h=G // 2 + 2 * Img, G=G)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -326,7 +327,7 @@ def run_ours(args):
     hbm = hbm or 6800.0
     per_launch_slices = plan.chunk
     kern = {}
-    for name in ("iir", "pass1_resample", "pass2"):
+    for name in ("iir", "pass1_resample", "pass2", "pass2_h"):
         ms, n = prof[name]
         if n:
             kern[name] = dict(ms_per_launch=ms / n, launches=n,

@@ -164,10 +164,11 @@ typedef enum {
     FBP_KERNEL_RESAMPLE = 1,       /* stand-alone resampling (fbp_resample_st) */
     FBP_KERNEL_PASS1_RESAMPLE = 2, /* resampling fused with the first Hough pass */
     FBP_KERNEL_PASS1_LINOGRAM = 3, /* first Hough pass reading a stored linogram */
-    FBP_KERNEL_PASS2 = 4,          /* second Hough pass fused with the quarter sum */
+    FBP_KERNEL_PASS2 = 4,          /* second Hough pass, v quarters (stores F_v- + F_v+) */
     FBP_KERNEL_FIR = 5,            /* comparator: exact FIR ramp */
     FBP_KERNEL_DIRECT_BP = 6,      /* comparator: pixel-driven back projection */
-    FBP_KERNEL_COUNT = 7
+    FBP_KERNEL_PASS2_H = 7,        /* second Hough pass, h quarters (adds F_h- + F_h+) */
+    FBP_KERNEL_COUNT = 8
 } fbp_kernel_id;
 
 /* Measurement hooks (no counterpart in the paper).  The plan always counts the kernels it

@@ -263,7 +263,8 @@ def fbp_reconstruct_host(plan: Plan, h_sino, h_img, count=None, stream=None) -> 
         int(count), _stream_ptr(stream)))
 
 
-KERNELS = ("iir", "resample", "pass1_resample", "pass1_linogram", "pass2", "fir", "direct_bp")
+KERNELS = ("iir", "resample", "pass1_resample", "pass1_linogram", "pass2", "fir", "direct_bp",
+           "pass2_h")
 
 
 def fbp_profile_enable(plan: Plan, enable: bool = True) -> None:

@@ -221,11 +221,7 @@ fbp_status build_iir_params(fbp_plan_s* p)
     return FBP_OK;
 }
 
-void split(double v, float& hi, float& lo)
-{
-    hi = (float)v;
-    lo = (float)(v - (double)hi);
-}
+long long to_fixed(double v) { return llround(ldexp(v, fbp::kFixBits)); }
 
 // Per (quarter, row) sampling geometry, computed in float64 (Sec. 4.1-4.2, Eq. 14-15).
 // Quarter order v-, v+, h-, h+; row i has slope sigma = i/(N-1).  Normal angle theta:
@@ -261,8 +257,8 @@ std::vector<fbp::RowGeom> build_geometry(int N, int K, int M)
             const double inv = 1.0 / sqrt(1.0 + s * s);
             double A = inv, B = -c0 * (1.0 + s) * inv;
             if (q == 3) { A = -A; B = -B; }
-            split(A, e.a_hi, e.a_lo);
-            split(B + half, e.b_hi, e.b_lo);
+            e.a_fx = to_fixed(A);
+            e.b_fx = to_fixed(B + half);
         }
     }
     return g;
@@ -357,7 +353,9 @@ cudaError_t reconstruct_chunk(fbp_plan_s* p, const float* sino, float* img, int 
         e = run(p, FBP_KERNEL_PASS1_RESAMPLE, st,
                 [&] { return fbp::launch_pass1(p, filt, false, g, cnt, st); });
     if (e == cudaSuccess)
-        e = run(p, FBP_KERNEL_PASS2, st, [&] { return fbp::launch_pass2(p, g, img, cnt, st); });
+        e = run(p, FBP_KERNEL_PASS2, st, [&] { return fbp::launch_pass2(p, g, img, cnt, false, st); });
+    if (e == cudaSuccess && p->n2 > 0)
+        e = run(p, FBP_KERNEL_PASS2_H, st, [&] { return fbp::launch_pass2(p, g, img, cnt, true, st); });
     return e;
 }
 
@@ -608,10 +606,11 @@ fbp_status fbp_fht_backproject(fbp_plan_t p, const float* d_lin, float* d_img, v
         cudaError_t e = run(p, FBP_KERNEL_PASS1_LINOGRAM, st, [&] {
             return fbp::launch_pass1(p, d_lin + (size_t)c * fbp::lin_floats(p), true, gbuf, cnt, st);
         });
+        float* img = d_img + (size_t)c * fbp::img_floats(p);
         if (e == cudaSuccess)
-            e = run(p, FBP_KERNEL_PASS2, st, [&] {
-                return fbp::launch_pass2(p, gbuf, d_img + (size_t)c * fbp::img_floats(p), cnt, st);
-            });
+            e = run(p, FBP_KERNEL_PASS2, st, [&] { return fbp::launch_pass2(p, gbuf, img, cnt, false, st); });
+        if (e == cudaSuccess && p->n2 > 0)
+            e = run(p, FBP_KERNEL_PASS2_H, st, [&] { return fbp::launch_pass2(p, gbuf, img, cnt, true, st); });
         if (e != cudaSuccess) return FBP_ERR_CUDA;
     }
     return FBP_OK;

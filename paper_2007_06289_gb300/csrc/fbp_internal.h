@@ -15,17 +15,19 @@ constexpr int kMaxOrder = FBP_MAX_ORDER;
 constexpr int kScanSteps = 5;            // log2(32 lanes)
 
 // Per linogram row (quarter q, slope row i): where the row samples the filtered sinogram.
-// Detector index m(c) = A*c + B for stored column c, carried as float pairs (hi + lo) so
-// that the fractional position keeps ~2^-24 absolute accuracy at |m| ~ 4096.
-// Angle index k0 + ft; the second angle row is k0+1, or row 0 with the detector mirrored
-// (m -> M-1-m) when k0+1 == K ("wrap", p(theta+pi, r) = p(theta, -r)).
+// Detector index m(c) = A*c + B for stored column c, carried in signed 64-bit fixed point
+// with kFixBits fractional bits: stepping c by one adds a_fx exactly, and the fraction of m
+// comes out with ~2^-24 absolute accuracy at |m| ~ 4096.  Angle index k0 + ft; the second
+// angle row is k0+1, or row 0 with the detector mirrored (m -> M-1-m) when k0+1 == K
+// ("wrap", p(theta+pi, r) = p(theta, -r)).
+constexpr int kFixBits = 40;
 struct RowGeom {
     int k0;
     int wrap;
     float ft;
     float w;        // row weight (trapezoid in sigma, Jacobian 1/k_t^2)
-    float a_hi, a_lo;
-    float b_hi, b_lo;
+    long long a_fx;
+    long long b_fx;
 };
 
 // The recursive filter in parallel (modal) form, as the kernel consumes it:
@@ -80,8 +82,10 @@ cudaError_t launch_resample(const fbp_plan_s* p, const float* filt, float* lin, 
                             cudaStream_t st);
 cudaError_t launch_pass1(const fbp_plan_s* p, const float* src, bool from_lin, float* g,
                          int count, cudaStream_t st);
+// Second pass: horizontal == false launches the v quarters (stores F_v- + F_v+),
+// horizontal == true the h quarters (adds F_h- + F_h+); the v launch must come first.
 cudaError_t launch_pass2(const fbp_plan_s* p, const float* g, float* img, int count,
-                         cudaStream_t st);
+                         bool horizontal, cudaStream_t st);
 cudaError_t launch_fir(const fbp_plan_s* p, const float* in, float* out, int rows,
                        cudaStream_t st);
 cudaError_t launch_direct_bp(const fbp_plan_s* p, const float* filt, float* img, int count,

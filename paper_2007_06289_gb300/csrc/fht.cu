@@ -10,6 +10,13 @@
 // (bit k-1 of r clear) with column shifts t and t+1, t = rev_{k-1}(r mod 2^(k-1)):
 //     out[r][u]           = in[r][u] + in[r + 2^(k-1)][u + t]
 //     out[r + 2^(k-1)][u] = in[r][u] + in[r + 2^(k-1)][u + t + 1]
+// Two consecutive stages act on quads of rows {a, a+h, a+2h, a+3h} (h = 2^(k-1), bits k-1
+// and k of a clear) with shifts t, t+1 and 2t, 2t+1, 2t+2, so they are done in registers
+// ("radix-4 rounds"): one shared-memory read and one write per element per two stages.
+// Quads touch disjoint rows, so a round runs in place: each quad belongs to one warp, which
+// sweeps its columns left to right in 128-column chunks (a chunk only reads columns that
+// later chunks write).
+//
 // Splitting n = n1 + n2, i = i_hi 2^n1 + i_lo, tau = tau_hi 2^n2 + tau_lo, the pattern
 // separates as d_tau(i) = d_{tau_hi}(i_lo) + tau_hi i_hi + d_{tau_lo}(i_hi), so the
 // transform runs in two passes, each a small transform in shared memory:
@@ -26,68 +33,81 @@
 namespace fbp {
 namespace {
 
-constexpr int kP1Threads = 256;
-constexpr int kP1Tile = 64;      // pass-1 output columns per CTA
-constexpr int kP2Threads = 256;
-constexpr int kP2Tile = 64;      // pass-2 image tile edge
+constexpr int kWB1 = 256;      // pass-1 tile width including the halo of 2^n1 columns
+constexpr int kNT1 = 512;      // pass-1 threads
+constexpr int kNT2 = 256;      // pass-2 threads
 
 __device__ __forceinline__ int rev_bits(int v, int bits)
 {
     return bits == 0 ? 0 : (int)(__brev((unsigned)v) >> (32 - bits));
 }
 
-// Detector position m = A*c + B in double-float, returned as integer part j and
-// fraction f in [0, 1).
-__device__ __forceinline__ void detector_pos(const RowGeom& g, int c, int& j, float& f)
+// Shared-memory column index with one pad word per 32 columns: a warp whose lanes hold
+// four consecutive columns each reads 32 distinct banks.
+__host__ __device__ constexpr int phys(int x) { return x + (x >> 5); }
+
+// Asynchronous 4-byte global -> shared copy; an invalid source writes 0.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid)
 {
-    const float cf = (float)c;
-    const float p = g.a_hi * cf;
-    const float pe = fmaf(g.a_hi, cf, -p);            // exact rounding error of the product
-    const float s = p + g.b_hi;
-    const float bb = s - p;
-    const float se = (p - (s - bb)) + (g.b_hi - bb);  // exact rounding error of the sum
-    const float lo = se + pe + fmaf(g.a_lo, cf, g.b_lo);
-    const float fl = floorf(s);
-    const float fr = (s - fl) + lo;                   // s - fl is exact
-    const float adj = floorf(fr);
-    j = (int)fl + (int)adj;
-    f = fr - adj;
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// ------------------------------------------------------------------------ resampling
+// Detector position in fixed point -> integer bin j and fraction f in [0, 1).
+__device__ __forceinline__ void split_fixed(long long m, int& j, float& f)
+{
+    j = (int)(m >> kFixBits);
+    const unsigned frac24 = (unsigned)(m >> (kFixBits - 24)) & 0xFFFFFFu;
+    f = (float)frac24 * (1.0f / 16777216.0f);
+}
+
+// Detector sample j of a row, zero outside [0, M); the load itself is never predicated
+// (clamped index), so a batch of them can be in flight together.
+__device__ __forceinline__ float ld_bin(const float* __restrict__ row, int M, int j)
+{
+    const int jc = min(max(j, 0), M - 1);
+    const float v = __ldg(row + jc);
+    return (unsigned)j < (unsigned)M ? v : 0.0f;
 }
 
 __device__ __forceinline__ float row_lerp(const float* __restrict__ row, int M, int j, float f)
 {
-    const float v0 = (j >= 0 && j < M) ? __ldg(row + j) : 0.0f;
-    const float v1 = (j + 1 >= 0 && j + 1 < M) ? __ldg(row + j + 1) : 0.0f;
+    const float v0 = ld_bin(row, M, j);
+    const float v1 = ld_bin(row, M, j + 1);
     return fmaf(f, v1 - v0, v0);
 }
 
-// One linogram sample: w * bilinear(p~, k0 + ft, m(c)).
+// One linogram sample at fixed-point detector position m: w * bilinear(p~, k0 + ft, m).
 __device__ __forceinline__ float linogram_sample(const RowGeom& g, const float* __restrict__ pt,
-                                                 int K, int M, int c)
+                                                 int M, long long m)
 {
     int j;
     float f;
-    detector_pos(g, c, j, f);
+    split_fixed(m, j, f);
     const float* rowa = pt + (size_t)g.k0 * M;
     const float va = row_lerp(rowa, M, j, f);
     float vb;
     if (!g.wrap) {
         vb = row_lerp(rowa + M, M, j, f);
     } else {
-        // p(pi + theta, r) = p(theta, -r): mirrored detector on row 0; m' = (M-1) - m
+        // p(pi + theta, r) = p(theta, -r): row 0 with the detector mirrored, m' = (M-1) - m
         int jm;
         float fm;
-        if (f == 0.0f) { jm = M - 1 - j; fm = 0.0f; }
-        else { jm = M - 2 - j; fm = 1.0f - f; }
+        split_fixed(((long long)(M - 1) << kFixBits) - m, jm, fm);
         vb = row_lerp(pt, M, jm, fm);
     }
-    (void)K;
     return g.w * fmaf(g.ft, vb - va, va);
 }
 
-// ---------------------------------------------------------------------------------------
 // Plain resampling into the stored linogram [count][4][N][2N] (every entry written).
-// ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 resample_kernel(const float* __restrict__ filt, float* __restrict__ lin,
                 const RowGeom* __restrict__ geom, int N, int K, int M)
@@ -99,61 +119,162 @@ resample_kernel(const float* __restrict__ filt, float* __restrict__ lin,
     if (c >= W) return;
     const RowGeom g = geom[qi];
     const float* pt = filt + (size_t)s * K * M;
-    lin[((size_t)s * 4 * N + qi) * W + c] = linogram_sample(g, pt, K, M, c);
+    lin[((size_t)s * 4 * N + qi) * W + c] = linogram_sample(g, pt, M, g.b_fx + g.a_fx * (long long)c);
 }
 
-// ---------------------------------------------------------------------------------------
-// Shared-memory Hough stages on R = 2^LOGR rows of width WB (bit-reversed slope rows).
-// Reads past column WB-1 are zero.  Returns the buffer holding the result.
-// ---------------------------------------------------------------------------------------
-template <int LOGR, int WB, int NT>
-__device__ __forceinline__ float* fht_stages_smem(float* cur, float* nxt)
+// ------------------------------------------------------------------------ Hough rounds
+// Stage 1 (shift 0) on row pairs (2m, 2m+1), in place, one warp per pair.
+template <int R, int WB, int PITCH, int NWARPS>
+__device__ __forceinline__ void round_r2(float* buf, int warp, int lane)
+{
+    const int p = phys(4 * lane);
+    const int p4 = phys(4 * lane + 4);
+    for (int pr = warp; pr < R / 2; pr += NWARPS) {
+#pragma unroll 1
+        for (int xb = 0; xb < WB; xb += 128) {
+            const bool act = xb + 4 * lane < WB;
+            float* A = buf + (2 * pr) * PITCH + phys(xb);
+            float* B = A + PITCH;
+            float a[4], b[5];
+            if (act) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) { a[k] = A[p + k]; b[k] = B[p + k]; }
+                b[4] = B[p4];
+            }
+            __syncwarp();
+            if (act) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    A[p + k] = a[k] + b[k];
+                    B[p + k] = a[k] + b[k + 1];
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Stages s and s+1 (h = 2^(s-1)) on row quads, in place, one warp per quad.
+template <int R, int WB, int PITCH, int NWARPS>
+__device__ __forceinline__ void round_r4(float* buf, int s, int warp, int lane)
+{
+    const int h = 1 << (s - 1);
+    for (int qd = warp; qd < R / 4; qd += NWARPS) {
+        const int qlo = qd & (h - 1);
+        const int a = ((qd >> (s - 1)) << (s + 1)) | qlo;
+        const int t = rev_bits(qlo, s - 1);
+        // phys(xb + y) = phys(xb) + phys(y) for xb a multiple of 32, so each lane's shifted
+        // offsets are computed once per quad and reused for every 128-column chunk.
+        int ob[5], oc[6], od[7];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) ob[k] = phys(4 * lane + t + k);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) oc[k] = phys(4 * lane + 2 * t + k);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) od[k] = phys(4 * lane + 3 * t + k);
+        const int pl = phys(4 * lane);
+#pragma unroll 1
+        for (int xb = 0; xb < WB; xb += 128) {
+            const int x0 = xb + 4 * lane;
+            const bool act = x0 < WB;
+            const int pb = phys(xb);
+            float* A = buf + a * PITCH + pb;
+            float* B = A + h * PITCH;
+            float* C = A + 2 * h * PITCH;
+            float* D = A + 3 * h * PITCH;
+            const int p = pl;
+            float o0[4], o1[4], o2[4], o3[4];          // rows a, a+h, a+2h, a+3h
+            if (act) {
+                float va[4], vb[5], vc[6], vd[7];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) va[k] = A[p + k];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) vb[k] = B[ob[k]];
+#pragma unroll
+                for (int k = 0; k < 6; ++k) vc[k] = C[oc[k]];
+#pragma unroll
+                for (int k = 0; k < 7; ++k) vd[k] = D[od[k]];
+                // stage s: rows a, a+h from (A, B) with shifts t, t+1; rows a+2h, a+3h from
+                // (C, D) likewise, at the columns stage s+1 will read
+                float x0v[4], x1v[4], y0[5], y1[5];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) { x0v[k] = va[k] + vb[k]; x1v[k] = va[k] + vb[k + 1]; }
+#pragma unroll
+                for (int k = 0; k < 5; ++k) { y0[k] = vc[k] + vd[k]; y1[k] = vc[k + 1] + vd[k + 2]; }
+                // stage s+1: pairs (a, a+2h) with shift 2t and (a+h, a+3h) with shift 2t+1
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    o0[k] = x0v[k] + y0[k];
+                    o2[k] = x0v[k] + y0[k + 1];
+                    o1[k] = x1v[k] + y1[k];
+                    o3[k] = x1v[k] + y1[k + 1];
+                }
+            }
+            __syncwarp();
+            if (act) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    A[p + k] = o0[k];
+                    B[p + k] = o1[k];
+                    C[p + k] = o2[k];
+                    D[p + k] = o3[k];
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// All LOGR stages on the R = 2^LOGR rows of `buf`; on return row j holds slope rev(j).
+template <int LOGR, int WB, int PITCH, int NWARPS>
+__device__ __forceinline__ void hough_stages(float* buf, int warp, int lane)
 {
     constexpr int R = 1 << LOGR;
-#pragma unroll 1
-    for (int s = 1; s <= LOGR; ++s) {
-        const int h = 1 << (s - 1);
-        for (int idx = threadIdx.x; idx < (R / 2) * WB; idx += NT) {
-            const int pr = idx / WB;
-            const int x = idx - pr * WB;
-            const int lo = pr & (h - 1);
-            const int r = ((pr >> (s - 1)) << s) | lo;
-            const int t = rev_bits(lo, s - 1);
-            const float a = cur[r * WB + x];
-            const int xb = x + t;
-            const float b0 = (xb < WB) ? cur[(r + h) * WB + xb] : 0.0f;
-            const float b1 = (xb + 1 < WB) ? cur[(r + h) * WB + xb + 1] : 0.0f;
-            nxt[r * WB + x] = a + b0;
-            nxt[(r + h) * WB + x] = a + b1;
-        }
+    int s = 1;
+    if (LOGR & 1) {
+        round_r2<R, WB, PITCH, NWARPS>(buf, warp, lane);
         __syncthreads();
-        float* tmp = cur;
-        cur = nxt;
-        nxt = tmp;
+        s = 2;
     }
-    return cur;
+#pragma unroll 1
+    for (; s < LOGR; s += 2) {
+        round_r4<R, WB, PITCH, NWARPS>(buf, s, warp, lane);
+        __syncthreads();
+    }
 }
 
+template <int R, int WB>
+constexpr int hough_pitch() { return phys(WB + 3 * (R / 4) + 8) + 1; }
+
+// Pass-2 shared floats: Hough rows, the first quarter's [T2][R+1] result, and for the h
+// quarters the [T2][R] image tile.
+template <int LOGR2, int T2, bool HORIZ>
+constexpr int pass2_floats()
+{
+    constexpr int R = 1 << LOGR2;
+    return R * hough_pitch<R, T2 + R>() + T2 * (R + 1) + (HORIZ ? T2 * R : 0);
+}
+
+// ------------------------------------------------------------------------ pass 1
 struct Pass1Args {
     const float* src;       // filtered sinogram [count][K][M] or linogram [count][4][N][2N]
     float* g;               // [count][4][N][2N]
     const RowGeom* geom;
     int N, K, M;
-    int n1;
 };
 
-// Pass 1: CTA = (column tile, quarter * blocks + block, slice).  Loads (or resamples) the
-// block's 2^LOGR linogram rows over the tile plus halo, runs LOGR stages, writes G.
+// CTA = (column tile, quarter * blocks + block, slice).  Resamples (or loads) the block's
+// 2^LOGR linogram rows over the tile plus halo, runs LOGR stages, writes G.
 template <int LOGR, bool FROM_LIN>
-__global__ void __launch_bounds__(kP1Threads)
+__global__ void __launch_bounds__(kNT1)
 pass1_kernel(Pass1Args a)
 {
     constexpr int R = 1 << LOGR;
-    constexpr int T = kP1Tile;
-    constexpr int WB = T + R;
-    extern __shared__ float smem[];
-    float* buf0 = smem;
-    float* buf1 = smem + R * WB;
+    constexpr int WB = kWB1;
+    constexpr int T = WB - R;
+    constexpr int PITCH = hough_pitch<R, WB>();
+    constexpr int NWARPS = kNT1 / 32;
+    extern __shared__ float buf[];
 
     const int N = a.N, W = 2 * N;
     const int nblocks = N >> LOGR;
@@ -162,106 +283,208 @@ pass1_kernel(Pass1Args a)
     const int s = blockIdx.z;
     const int c0 = blockIdx.x * T;
     if (c0 >= N + R * bi) return;                      // nothing needed in this tile
-
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const size_t lin_q = ((size_t)s * 4 + q) * N;      // row index base of this quarter
-    for (int idx = threadIdx.x; idx < R * WB; idx += kP1Threads) {
-        const int j = idx / WB;
-        const int x = idx - j * WB;
-        const int i = bi * R + j;
-        const int c = c0 + x;
-        float v = 0.0f;
-        if (c <= N - 1 + i && c < W) {
-            if (FROM_LIN) {
-                v = a.src[(lin_q + i) * W + c];
-            } else {
-                const RowGeom gm = a.geom[q * N + i];
-                v = linogram_sample(gm, a.src + (size_t)s * a.K * a.M, a.K, a.M, c);
+
+    if (FROM_LIN) {
+        for (int idx = threadIdx.x; idx < R * WB; idx += kNT1) {
+            const int j = idx / WB;
+            const int x = idx - j * WB;
+            const int i = bi * R + j;
+            const int c = c0 + x;
+            const bool ok = c <= N - 1 + i;
+            cp_async4(buf + j * PITCH + phys(x), ok ? a.src + (lin_q + i) * W + c : a.src, ok);
+        }
+    } else {
+        // One warp per linogram row, lane = column within each 32-column group.  Each batch
+        // of kS samples issues all of its gathers before combining any of them; the
+        // arithmetic is the same as linogram_sample's, term for term.
+        const float* pt = a.src + (size_t)s * a.K * a.M;
+        const int M = a.M;
+        constexpr int kS = 4;
+        for (int j = warp; j < R; j += NWARPS) {
+            const int i = bi * R + j;
+            const int limit = N - 1 + i;
+            float* row = buf + j * PITCH + lane;
+            if (c0 > limit) {                                  // tile past the trapezoid
+#pragma unroll
+                for (int k = 0; k < WB / 32; ++k) row[33 * k] = 0.0f;
+                continue;
+            }
+            const RowGeom gm = a.geom[q * N + i];
+            const float* ra = pt + (size_t)gm.k0 * M;
+            const long long m0 = gm.b_fx + gm.a_fx * (long long)(c0 + lane);
+            const long long step = gm.a_fx * 32;
+            if (!gm.wrap) {
+                // Angle rows k0 and k0+1 are adjacent: one clamped address serves all four
+                // bins; the selects restore the zero padding outside [0, M).
+                long long m = m0;
+#pragma unroll
+                for (int kb = 0; kb < WB / 32; kb += kS) {
+                    float l0[kS], l1[kS], l2[kS], l3[kS], fr[kS];
+                    int dd[kS];
+#pragma unroll
+                    for (int k = 0; k < kS; ++k, m += step) {
+                        int j;
+                        split_fixed(m, j, fr[k]);
+                        const int jc = min(max(j, 0), M - 2);
+                        dd[k] = j - jc;
+                        const float* pp = ra + jc;
+                        l0[k] = __ldg(pp);
+                        l1[k] = __ldg(pp + 1);
+                        l2[k] = __ldg(pp + M);
+                        l3[k] = __ldg(pp + M + 1);
+                    }
+#pragma unroll
+                    for (int k = 0; k < kS; ++k) {
+                        const int d = dd[k];
+                        const float a0 = d == 0 ? l0[k] : (d == 1 ? l1[k] : 0.0f);
+                        const float a1 = d == 0 ? l1[k] : (d == -1 ? l0[k] : 0.0f);
+                        const float b0 = d == 0 ? l2[k] : (d == 1 ? l3[k] : 0.0f);
+                        const float b1 = d == 0 ? l3[k] : (d == -1 ? l2[k] : 0.0f);
+                        const float va = fmaf(fr[k], a1 - a0, a0);
+                        const float vb = fmaf(fr[k], b1 - b0, b0);
+                        const float v = gm.w * fmaf(gm.ft, vb - va, va);
+                        row[33 * (kb + k)] = (c0 + lane + 32 * (kb + k) <= limit) ? v : 0.0f;
+                    }
+                }
+                continue;
+            }
+            const float* rb = pt;                              // wrap: row 0, mirrored
+            const long long mirror = ((long long)(M - 1) << kFixBits);
+#pragma unroll
+            for (int kb = 0; kb < WB / 32; kb += kS) {
+                float a0[kS], a1[kS], b0[kS], b1[kS], fa[kS], fb[kS];
+#pragma unroll
+                for (int k = 0; k < kS; ++k) {
+                    const long long m = m0 + step * (kb + k);
+                    int ja, jb;
+                    split_fixed(m, ja, fa[k]);
+                    if (gm.wrap) split_fixed(mirror - m, jb, fb[k]);
+                    else { jb = ja; fb[k] = fa[k]; }
+                    a0[k] = ld_bin(ra, M, ja);
+                    a1[k] = ld_bin(ra, M, ja + 1);
+                    b0[k] = ld_bin(rb, M, jb);
+                    b1[k] = ld_bin(rb, M, jb + 1);
+                }
+#pragma unroll
+                for (int k = 0; k < kS; ++k) {
+                    const float va = fmaf(fa[k], a1[k] - a0[k], a0[k]);
+                    const float vb = fmaf(fb[k], b1[k] - b0[k], b0[k]);
+                    const float v = gm.w * fmaf(gm.ft, vb - va, va);
+                    row[33 * (kb + k)] = (c0 + lane + 32 * (kb + k) <= limit) ? v : 0.0f;
+                }
             }
         }
-        buf0[idx] = v;
     }
+    for (int j = warp; j < R; j += NWARPS)
+        for (int p = phys(WB) + lane; p < PITCH; p += 32) buf[j * PITCH + p] = 0.0f;
+    if (FROM_LIN) cp_async_wait_all();
     __syncthreads();
-    const float* res = fht_stages_smem<LOGR, WB, kP1Threads>(buf0, buf1);
 
-    for (int idx = threadIdx.x; idx < R * T; idx += kP1Threads) {
+    hough_stages<LOGR, WB, PITCH, NWARPS>(buf, warp, lane);
+
+    for (int idx = threadIdx.x; idx < R * T; idx += kNT1) {
         const int j = idx / T;
         const int x = idx - j * T;
         const int tau = rev_bits(j, LOGR);
         const int c = c0 + x;
         if (c < N + (tau + 1) * bi)
-            a.g[(lin_q + (size_t)bi * R + tau) * W + c] = res[j * WB + x];
+            a.g[(lin_q + (size_t)bi * R + tau) * W + c] = buf[j * PITCH + phys(x)];
     }
 }
 
+// ------------------------------------------------------------------------ pass 2
 struct Pass2Args {
     const float* g;         // [count][4][N][2N]
     float* img;             // [count][N][N]
     int N, n1;
 };
 
-// Pass 2 + quarter sum: CTA = (image tile x, image tile y, slice).  For each quarter and
-// each slope group tau_hi covering the tile, loads the sheared G rows, runs LOGR2 stages
-// and scatters the quarter image into the tile: v quarters as [y][x], h quarters
-// transposed, '+' quarters mirrored.  f = (F_v- + F_v+) + (F_h- + F_h+).
-template <int LOGR2>
-__global__ void __launch_bounds__(kP2Threads)
+// CTA = (tile of T2 intercepts u, slope group tau_hi, slice).  Runs the second pass for the
+// '-' quarter on u in [x0, x0+T2) and for the '+' quarter on the mirrored range, adds them
+// (F_- + F_+), and either stores the sum into the image (v quarters: [y = tau][x = u]) or
+// adds it to the image through a shared-memory transpose (h quarters: [y = u][x = tau]).
+// Launched for the v quarters first and the h quarters second, so each pixel ends as
+// (F_v- + F_v+) + (F_h- + F_h+).
+template <int LOGR2, int T2, bool HORIZ>
+__global__ void __launch_bounds__(kNT2)
 pass2_kernel(Pass2Args a)
 {
-    constexpr int R2 = 1 << LOGR2;
-    constexpr int TL = kP2Tile;
-    constexpr int WB = TL + R2;
-    constexpr int TP = TL + 1;               // padded tile row
-    extern __shared__ float smem[];
-    float* buf0 = smem;
-    float* buf1 = buf0 + R2 * WB;
-    float* sv = buf1 + R2 * WB;              // [TL][TP]  F_v- + F_v+
-    float* sh = sv + TL * TP;                // [TL][TP]  F_h- + F_h+
+    constexpr int R = 1 << LOGR2;
+    constexpr int WB = T2 + R;                 // two 128-column chunks
+    constexpr int PITCH = hough_pitch<R, WB>();
+    constexpr int NWARPS = kNT2 / 32;
+    constexpr int TP = R + 1;                  // [T2][R + 1] transposed tile (h quarters)
+    extern __shared__ float buf[];
 
     const int N = a.N, W = 2 * N;
     const int R1 = 1 << a.n1;
-    const int x0 = blockIdx.x * TL;
-    const int y0 = blockIdx.y * TL;
+    const int x0 = blockIdx.x * T2;            // the last tile may run past N
+    const int nx = min(T2, N - x0);            // intercepts of this tile inside the image
+    const int tau_hi = blockIdx.y;
     const int s = blockIdx.z;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* img = a.img + (size_t)s * N * N;
 
-    for (int q = 0; q < 4; ++q) {
-        const float* gq = a.g + ((size_t)s * 4 + q) * N * W;
-        const int tau_base = (q < 2) ? y0 : x0;
-        int uo;
-        if (q == 0) uo = x0;
-        else if (q == 1) uo = N - x0 - TL;
-        else if (q == 2) uo = y0;
-        else uo = N - y0 - TL;
-        for (int grp = 0; grp < TL / R2; ++grp) {
-            const int tau_hi = tau_base / R2 + grp;
-            for (int idx = threadIdx.x; idx < R2 * WB; idx += kP2Threads) {
-                const int ih = idx / WB;
-                const int x = idx - ih * WB;
-                const int col = uo + tau_hi * ih + x;
-                float v = 0.0f;
-                if (col < N + (tau_hi + 1) * ih)
-                    v = gq[((size_t)ih * R1 + tau_hi) * W + col];
-                buf0[idx] = v;
-            }
-            __syncthreads();
-            const float* res = fht_stages_smem<LOGR2, WB, kP2Threads>(buf0, buf1);
-            for (int idx = threadIdx.x; idx < R2 * TL; idx += kP2Threads) {
-                const int j = idx / TL;
-                const int xx = idx - j * TL;
-                const int t = grp * R2 + rev_bits(j, LOGR2);   // tau - tau_base
-                const float v = res[j * WB + xx];
-                if (q == 0) sv[t * TP + xx] = v;
-                else if (q == 1) sv[t * TP + (TL - 1 - xx)] += v;
-                else if (q == 2) sh[xx * TP + t] = v;
-                else sh[(TL - 1 - xx) * TP + t] += v;
-            }
-            __syncthreads();
+    // Shared layout: Hough rows | first-quarter result | (h only) the stored v tile.
+    float* first = buf + R * PITCH;                        // T2 * (R + 1) floats
+    float* vtile = first + T2 * TP;
+    // h quarters add to the image tile [y = x0 .. x0+nx) x [x = tau_hi R .. +R) that the v
+    // launch stored: fetch it now, behind the Hough work.
+    if (HORIZ) {
+        for (int e = threadIdx.x; e < nx * R; e += kNT2) {
+            const int xx = e / R;
+            const int tl = e - xx * R;
+            cp_async4(vtile + e, img + (size_t)(x0 + xx) * N + tau_hi * R + tl, true);
         }
     }
-    float* out = a.img + (size_t)s * N * N;
-    for (int idx = threadIdx.x; idx < TL * TL; idx += kP2Threads) {
-        const int yy = idx / TL;
-        const int xx = idx - yy * TL;
-        out[(size_t)(y0 + yy) * N + x0 + xx] = sv[yy * TP + xx] + sh[yy * TP + xx];
+
+#pragma unroll 1
+    for (int half = 0; half < 2; ++half) {
+        const int q = (HORIZ ? 2 : 0) + half;
+        // '-' quarter: u = x0 + xx; '+' quarter: u = N-1-(x0+xx), i.e. column T2-1-xx of a
+        // tile starting at N - x0 - T2 (negative for a partial last tile: those columns
+        // only feed intercepts outside the image)
+        const int uo = half == 0 ? x0 : N - x0 - T2;
+        const float* gq = a.g + ((size_t)s * 4 + q) * N * W;
+        for (int idx = threadIdx.x; idx < R * WB; idx += kNT2) {
+            const int ih = idx / WB;
+            const int x = idx - ih * WB;
+            const int col = uo + tau_hi * ih + x;
+            const bool ok = col >= 0 && col < N + (tau_hi + 1) * ih;
+            cp_async4(buf + ih * PITCH + phys(x), ok ? gq + ((size_t)ih * R1 + tau_hi) * W + col : gq, ok);
+        }
+        for (int j = warp; j < R; j += NWARPS)
+            for (int p = phys(WB) + lane; p < PITCH; p += 32) buf[j * PITCH + p] = 0.0f;
+        cp_async_wait_all();
+        __syncthreads();
+
+        hough_stages<LOGR2, WB, PITCH, NWARPS>(buf, warp, lane);
+
+        // first quarter: park F_- at [xx][tau_lo]; second quarter: F_- + F_+, stored to the
+        // image rows (v) or accumulated in place for the transposed write (h)
+        for (int e = threadIdx.x; e < R * T2; e += kNT2) {
+            const int j = e / T2;
+            const int xx = e - j * T2;
+            float* f = first + xx * TP + rev_bits(j, LOGR2);
+            if (half == 0) {
+                *f = buf[j * PITCH + phys(xx)];
+            } else {
+                const float v = *f + buf[j * PITCH + phys(T2 - 1 - xx)];
+                if (HORIZ) *f = v;
+                else if (xx < nx) img[(size_t)(tau_hi * R + rev_bits(j, LOGR2)) * N + x0 + xx] = v;
+            }
+        }
+        __syncthreads();
+    }
+
+    if (HORIZ) {
+        for (int e = threadIdx.x; e < nx * R; e += kNT2) {
+            const int xx = e / R;
+            const int tl = e - xx * R;
+            img[(size_t)(x0 + xx) * N + tau_hi * R + tl] = vtile[e] + first[xx * TP + tl];
+        }
     }
 }
 
@@ -282,36 +505,34 @@ combine_kernel(const float* __restrict__ g, float* __restrict__ img, int N)
     img[(size_t)s * N * N + p] = v + hh;
 }
 
-template <int LOGR, bool FROM_LIN>
-size_t pass1_smem() { return (size_t)2 * (1 << LOGR) * (kP1Tile + (1 << LOGR)) * sizeof(float); }
+// ------------------------------------------------------------------------ launchers
+template <int LOGR>
+constexpr size_t pass1_smem() { return (size_t)(1 << LOGR) * hough_pitch<(1 << LOGR), kWB1>() * sizeof(float); }
 
-template <int LOGR2>
-size_t pass2_smem()
-{
-    return ((size_t)2 * (1 << LOGR2) * (kP2Tile + (1 << LOGR2)) + 2 * kP2Tile * (kP2Tile + 1)) *
-           sizeof(float);
-}
+template <int LOGR2, int T2, bool HORIZ>
+constexpr size_t pass2_smem() { return (size_t)pass2_floats<LOGR2, T2, HORIZ>() * sizeof(float); }
 
 template <int LOGR, bool FROM_LIN>
 cudaError_t launch_pass1_t(const fbp_plan_s* p, const float* src, float* g, int count,
                            cudaStream_t st)
 {
-    const int R = 1 << LOGR;
+    constexpr int R = 1 << LOGR;
+    constexpr int T = kWB1 - R;
     const int nblocks = p->N >> LOGR;
     const int max_cols = p->N + R * (nblocks - 1);
-    dim3 grid((max_cols + kP1Tile - 1) / kP1Tile, 4 * nblocks, count);
-    Pass1Args a{src, g, p->d_geom, p->N, p->K, p->M, p->n1};
-    pass1_kernel<LOGR, FROM_LIN><<<grid, kP1Threads, pass1_smem<LOGR, FROM_LIN>(), st>>>(a);
+    dim3 grid((max_cols + T - 1) / T, 4 * nblocks, count);
+    Pass1Args a{src, g, p->d_geom, p->N, p->K, p->M};
+    pass1_kernel<LOGR, FROM_LIN><<<grid, kNT1, pass1_smem<LOGR>(), st>>>(a);
     return cudaGetLastError();
 }
 
-template <int LOGR2>
+template <int LOGR2, int T2, bool HORIZ>
 cudaError_t launch_pass2_t(const fbp_plan_s* p, const float* g, float* img, int count,
                            cudaStream_t st)
 {
-    dim3 grid(p->N / kP2Tile, p->N / kP2Tile, count);
+    dim3 grid((p->N + T2 - 1) / T2, p->N >> LOGR2, count);
     Pass2Args a{g, img, p->N, p->n1};
-    pass2_kernel<LOGR2><<<grid, kP2Threads, pass2_smem<LOGR2>(), st>>>(a);
+    pass2_kernel<LOGR2, T2, HORIZ><<<grid, kNT2, pass2_smem<LOGR2, T2, HORIZ>(), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -319,15 +540,26 @@ template <int LOGR, bool FROM_LIN>
 cudaError_t set_p1_attr()
 {
     return cudaFuncSetAttribute(pass1_kernel<LOGR, FROM_LIN>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pass1_smem<LOGR, FROM_LIN>());
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pass1_smem<LOGR>());
 }
 
-template <int LOGR2>
+template <int LOGR2, int T2, bool HORIZ>
 cudaError_t set_p2_attr()
 {
-    return cudaFuncSetAttribute(pass2_kernel<LOGR2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pass2_smem<LOGR2>());
+    return cudaFuncSetAttribute(pass2_kernel<LOGR2, T2, HORIZ>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pass2_smem<LOGR2, T2, HORIZ>());
+}
+
+// Second-pass tile: T2 intercepts plus the 2^n2 halo fill exactly two 128-column chunks.
+template <int LOGR2>
+constexpr int pass2_tile() { return 256 - (1 << LOGR2); }
+
+template <int LOGR2, bool HORIZ>
+cudaError_t launch_pass2_n(const fbp_plan_s* p, const float* g, float* img, int count,
+                           cudaStream_t st)
+{
+    return launch_pass2_t<LOGR2, pass2_tile<LOGR2>(), HORIZ>(p, g, img, count, st);
 }
 
 }  // namespace
@@ -340,8 +572,9 @@ cudaError_t prepare_fht_kernels()
     if (e == cudaSuccess) e = set_p1_attr<L, true>();
     FBP_P1(1) FBP_P1(2) FBP_P1(3) FBP_P1(4) FBP_P1(5) FBP_P1(6)
 #undef FBP_P1
-#define FBP_P2(L) \
-    if (e == cudaSuccess) e = set_p2_attr<L>();
+#define FBP_P2(L)                                                      \
+    if (e == cudaSuccess) e = set_p2_attr<L, pass2_tile<L>(), false>();  \
+    if (e == cudaSuccess) e = set_p2_attr<L, pass2_tile<L>(), true>();
     FBP_P2(1) FBP_P2(2) FBP_P2(3) FBP_P2(4) FBP_P2(5) FBP_P2(6)
 #undef FBP_P2
     return e;
@@ -371,21 +604,21 @@ cudaError_t launch_pass1(const fbp_plan_s* p, const float* src, bool from_lin, f
 }
 
 cudaError_t launch_pass2(const fbp_plan_s* p, const float* g, float* img, int count,
-                         cudaStream_t st)
+                         bool horizontal, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
     if (p->n2 == 0) {
+        if (horizontal) return cudaSuccess;            // the sum kernel does all quarters
         dim3 grid((p->N * p->N + 255) / 256, count);
         combine_kernel<<<grid, 256, 0, st>>>(g, img, p->N);
         return cudaGetLastError();
     }
-    switch (p->n2) {
-        case 1: return launch_pass2_t<1>(p, g, img, count, st);
-        case 2: return launch_pass2_t<2>(p, g, img, count, st);
-        case 3: return launch_pass2_t<3>(p, g, img, count, st);
-        case 4: return launch_pass2_t<4>(p, g, img, count, st);
-        case 5: return launch_pass2_t<5>(p, g, img, count, st);
-        case 6: return launch_pass2_t<6>(p, g, img, count, st);
+    switch (p->n2 * 2 + (horizontal ? 1 : 0)) {
+#define FBP_C(L)                                                              \
+    case 2 * L: return launch_pass2_n<L, false>(p, g, img, count, st);       \
+    case 2 * L + 1: return launch_pass2_n<L, true>(p, g, img, count, st);
+        FBP_C(1) FBP_C(2) FBP_C(3) FBP_C(4) FBP_C(5) FBP_C(6)
+#undef FBP_C
         default: return cudaErrorInvalidValue;
     }
 }

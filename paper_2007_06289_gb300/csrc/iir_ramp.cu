@@ -129,7 +129,12 @@ iir_ramp_kernel(const float* in, float* out, int rows, int M, int warps_per_cta,
     float* sp = smem + (size_t)warp * 2 * M;              // input row
     float* sy = sp + M;                                    // result row
     const float* src = in + row * (long long)M;
-    for (int n = lane; n < M; n += 32) sp[n] = src[n];
+    // every element of the row in flight at once: asynchronous 4-byte copies into shared
+    for (int n = lane; n < M; n += 32) {
+        const unsigned d = (unsigned)__cvta_generic_to_shared(sp + n);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src + n) : "memory");
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncwarp();
 
     const int L = prm.L;
@@ -137,29 +142,76 @@ iir_ramp_kernel(const float* in, float* out, int rows, int M, int warps_per_cta,
     const int n1 = min(n0 + L, M);
     const int nd = prm.nd;
     ModeState<JR, JC> s;
-
-    // causal
-    zero_state(s);
-    for (int n = n0; n < n1; ++n) step(s, prm, sp[n]);
-    carry_scan<JR, JC, true>(s, prm, lane);
-    for (int n = n0; n < n1; ++n) {
-        step(s, prm, sp[n]);
+    // The recurrences read the chunk in blocks of kB samples fetched ahead into registers,
+    // so shared-memory latency stays off the dependency chain.
+    constexpr int kB = 8;
+    auto causal_out = [&](int n) {
         float y = output(s, prm);
         for (int k = 0; k < nd; ++k)
             if (n - k >= 0) y = fmaf(prm.d[k], sp[n - k], y);
         sy[n] = y;
-    }
-
-    // anticausal
-    zero_state(s);
-    for (int n = n1 - 1; n >= n0; --n) step(s, prm, sp[n]);
-    carry_scan<JR, JC, false>(s, prm, lane);
-    for (int n = n1 - 1; n >= n0; --n) {
-        step(s, prm, sp[n]);
+    };
+    auto anticausal_out = [&](int n) {
         float z = output(s, prm);
         for (int k = 0; k < nd; ++k)
             if (n + k < M) z = fmaf(prm.d[k], sp[n + k], z);
         sy[n] += z;
+    };
+
+    // causal: local pass from zero state, carry scan, final pass
+    zero_state(s);
+    int n = n0;
+    for (; n + kB <= n1; n += kB) {
+        float x[kB];
+#pragma unroll
+        for (int k = 0; k < kB; ++k) x[k] = sp[n + k];
+#pragma unroll
+        for (int k = 0; k < kB; ++k) step(s, prm, x[k]);
+    }
+    for (; n < n1; ++n) step(s, prm, sp[n]);
+    carry_scan<JR, JC, true>(s, prm, lane);
+    n = n0;
+    for (; n + kB <= n1; n += kB) {
+        float x[kB];
+#pragma unroll
+        for (int k = 0; k < kB; ++k) x[k] = sp[n + k];
+#pragma unroll
+        for (int k = 0; k < kB; ++k) {
+            step(s, prm, x[k]);
+            causal_out(n + k);
+        }
+    }
+    for (; n < n1; ++n) {
+        step(s, prm, sp[n]);
+        causal_out(n);
+    }
+
+    // anticausal: the same, walking the chunk backwards
+    zero_state(s);
+    n = n1 - 1;
+    for (; n - kB + 1 >= n0; n -= kB) {
+        float x[kB];
+#pragma unroll
+        for (int k = 0; k < kB; ++k) x[k] = sp[n - k];
+#pragma unroll
+        for (int k = 0; k < kB; ++k) step(s, prm, x[k]);
+    }
+    for (; n >= n0; --n) step(s, prm, sp[n]);
+    carry_scan<JR, JC, false>(s, prm, lane);
+    n = n1 - 1;
+    for (; n - kB + 1 >= n0; n -= kB) {
+        float x[kB];
+#pragma unroll
+        for (int k = 0; k < kB; ++k) x[k] = sp[n - k];
+#pragma unroll
+        for (int k = 0; k < kB; ++k) {
+            step(s, prm, x[k]);
+            anticausal_out(n - k);
+        }
+    }
+    for (; n >= n0; --n) {
+        step(s, prm, sp[n]);
+        anticausal_out(n);
     }
     __syncwarp();
 

@@ -87,7 +87,8 @@ extern "C" fbp_status fbp_fht_backproject_static(int N, int count, const float* 
     // that the second pass reads, so nothing has to be cleared between calls.
     for (int s = 0; s < count; ++s) {
         cudaError_t e = fbp::launch_pass1(&shape, d_lin + (size_t)s * lin, true, scratch, 1, st);
-        if (e == cudaSuccess) e = fbp::launch_pass2(&shape, scratch, d_img + (size_t)s * img, 1, st);
+        if (e == cudaSuccess) e = fbp::launch_pass2(&shape, scratch, d_img + (size_t)s * img, 1, false, st);
+        if (e == cudaSuccess) e = fbp::launch_pass2(&shape, scratch, d_img + (size_t)s * img, 1, true, st);
         if (e != cudaSuccess) return FBP_ERR_CUDA;
     }
     return FBP_OK;
