@@ -28,6 +28,8 @@
 // Only outputs u < N are needed; they read linogram row i at columns c <= N-1+i and
 // G[i_hi][tau_hi] at columns v < N + (tau_hi+1) i_hi.  Loads beyond these bounds read 0,
 // and tiles entirely beyond them are skipped: neither changes a needed output.
+#include <type_traits>
+
 #include "fbp_internal.h"
 
 namespace fbp {
@@ -123,9 +125,21 @@ resample_kernel(const float* __restrict__ filt, float* __restrict__ lin,
 }
 
 // ------------------------------------------------------------------------ Hough rounds
+// A round hands each thread's results -- four consecutive columns x0..x0+3 of one row --
+// to a sink.  SmemSink writes them back in place (every round but a pass's last); a pass
+// may give its last round a sink that stores straight to global memory.
+struct SmemSink {};
+
+template <int PITCH>
+__device__ __forceinline__ void smem_put(float* row, int p, const float (&o)[4])
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) row[p + k] = o[k];
+}
+
 // Stage 1 (shift 0) on row pairs (2m, 2m+1), in place, one warp per pair.
-template <int R, int WB, int PITCH, int NWARPS>
-__device__ __forceinline__ void round_r2(float* buf, int warp, int lane)
+template <int R, int WB, int PITCH, int NWARPS, class Sink>
+__device__ __forceinline__ void round_r2(float* buf, int warp, int lane, const Sink& sink)
 {
     const int p = phys(4 * lane);
     const int p4 = phys(4 * lane + 4);
@@ -143,10 +157,18 @@ __device__ __forceinline__ void round_r2(float* buf, int warp, int lane)
             }
             __syncwarp();
             if (act) {
+                float oa[4], ob[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    A[p + k] = a[k] + b[k];
-                    B[p + k] = a[k] + b[k + 1];
+                    oa[k] = a[k] + b[k];
+                    ob[k] = a[k] + b[k + 1];
+                }
+                if constexpr (std::is_same<Sink, SmemSink>::value) {
+                    smem_put<PITCH>(A, p, oa);
+                    smem_put<PITCH>(B, p, ob);
+                } else {
+                    sink(2 * pr, xb + 4 * lane, oa);
+                    sink(2 * pr + 1, xb + 4 * lane, ob);
                 }
             }
             __syncwarp();
@@ -155,8 +177,8 @@ __device__ __forceinline__ void round_r2(float* buf, int warp, int lane)
 }
 
 // Stages s and s+1 (h = 2^(s-1)) on row quads, in place, one warp per quad.
-template <int R, int WB, int PITCH, int NWARPS>
-__device__ __forceinline__ void round_r4(float* buf, int s, int warp, int lane)
+template <int R, int WB, int PITCH, int NWARPS, class Sink>
+__device__ __forceinline__ void round_r4(float* buf, int s, int warp, int lane, const Sink& sink)
 {
     const int h = 1 << (s - 1);
     for (int qd = warp; qd < R / 4; qd += NWARPS) {
@@ -212,12 +234,16 @@ __device__ __forceinline__ void round_r4(float* buf, int s, int warp, int lane)
             }
             __syncwarp();
             if (act) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    A[p + k] = o0[k];
-                    B[p + k] = o1[k];
-                    C[p + k] = o2[k];
-                    D[p + k] = o3[k];
+                if constexpr (std::is_same<Sink, SmemSink>::value) {
+                    smem_put<PITCH>(A, p, o0);
+                    smem_put<PITCH>(B, p, o1);
+                    smem_put<PITCH>(C, p, o2);
+                    smem_put<PITCH>(D, p, o3);
+                } else {
+                    sink(a, x0, o0);
+                    sink(a + h, x0, o1);
+                    sink(a + 2 * h, x0, o2);
+                    sink(a + 3 * h, x0, o3);
                 }
             }
             __syncwarp();
@@ -225,20 +251,29 @@ __device__ __forceinline__ void round_r4(float* buf, int s, int warp, int lane)
     }
 }
 
-// All LOGR stages on the R = 2^LOGR rows of `buf`; on return row j holds slope rev(j).
-template <int LOGR, int WB, int PITCH, int NWARPS>
-__device__ __forceinline__ void hough_stages(float* buf, int warp, int lane)
+// All LOGR stages on the R = 2^LOGR rows of `buf`; row j holds slope rev(j).  The last
+// round hands its results to `sink` (SmemSink: back into `buf`).
+template <int LOGR, int WB, int PITCH, int NWARPS, class Sink>
+__device__ __forceinline__ void hough_stages(float* buf, int warp, int lane, const Sink& sink)
 {
     constexpr int R = 1 << LOGR;
-    int s = 1;
-    if (LOGR & 1) {
-        round_r2<R, WB, PITCH, NWARPS>(buf, warp, lane);
+    const SmemSink in_place;
+    if constexpr (LOGR == 1) {
+        round_r2<R, WB, PITCH, NWARPS>(buf, warp, lane, sink);
         __syncthreads();
-        s = 2;
-    }
+    } else {
+        int s = 1;
+        if (LOGR & 1) {
+            round_r2<R, WB, PITCH, NWARPS>(buf, warp, lane, in_place);
+            __syncthreads();
+            s = 2;
+        }
 #pragma unroll 1
-    for (; s < LOGR; s += 2) {
-        round_r4<R, WB, PITCH, NWARPS>(buf, s, warp, lane);
+        for (; s + 2 < LOGR; s += 2) {
+            round_r4<R, WB, PITCH, NWARPS>(buf, s, warp, lane, in_place);
+            __syncthreads();
+        }
+        round_r4<R, WB, PITCH, NWARPS>(buf, s, warp, lane, sink);
         __syncthreads();
     }
 }
@@ -256,6 +291,28 @@ constexpr int pass2_floats()
 }
 
 // ------------------------------------------------------------------------ pass 1
+// Last-round sink of pass 1: slot row j holds slope tau = rev(j); its columns c0 + x0..+3
+// go straight to G row tau of the block, within the region the second pass reads.
+struct GSink {
+    float* rows;        // G row 0 of this (slice, quarter, block)
+    int W, T, c0, N, bi, logr;
+    __device__ __forceinline__ void operator()(int j, int x0, const float (&o)[4]) const
+    {
+        if (x0 >= T) return;                           // halo columns: not outputs
+        const int tau = rev_bits(j, logr);
+        const int c = c0 + x0;
+        const int need = N + (tau + 1) * bi;
+        float* dst = rows + (size_t)tau * W + c;
+        if ((c & 3) == 0 && c + 4 <= need) {
+            *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (c + k < need) dst[k] = o[k];
+        }
+    }
+};
+
 struct Pass1Args {
     const float* src;       // filtered sinogram [count][K][M] or linogram [count][4][N][2N]
     float* g;               // [count][4][N][2N]
@@ -382,16 +439,8 @@ pass1_kernel(Pass1Args a)
     if (FROM_LIN) cp_async_wait_all();
     __syncthreads();
 
-    hough_stages<LOGR, WB, PITCH, NWARPS>(buf, warp, lane);
-
-    for (int idx = threadIdx.x; idx < R * T; idx += kNT1) {
-        const int j = idx / T;
-        const int x = idx - j * T;
-        const int tau = rev_bits(j, LOGR);
-        const int c = c0 + x;
-        if (c < N + (tau + 1) * bi)
-            a.g[(lin_q + (size_t)bi * R + tau) * W + c] = buf[j * PITCH + phys(x)];
-    }
+    const GSink out{a.g + (lin_q + (size_t)bi * R) * W, W, T, c0, N, bi, LOGR};
+    hough_stages<LOGR, WB, PITCH, NWARPS>(buf, warp, lane, out);
 }
 
 // ------------------------------------------------------------------------ pass 2
@@ -460,7 +509,7 @@ pass2_kernel(Pass2Args a)
         cp_async_wait_all();
         __syncthreads();
 
-        hough_stages<LOGR2, WB, PITCH, NWARPS>(buf, warp, lane);
+        hough_stages<LOGR2, WB, PITCH, NWARPS>(buf, warp, lane, SmemSink{});
 
         // first quarter: park F_- at [xx][tau_lo]; second quarter: F_- + F_+, stored to the
         // image rows (v) or accumulated in place for the transposed write (h)
