@@ -123,18 +123,38 @@ fbp_status build_iir_params(fbp_plan_s* p)
 {
     fbp::IirParams& prm = p->iir;
     memset(&prm, 0, sizeof(prm));
-    int L = (p->M + 31) / 32;
-    if ((L & 1) == 0) ++L;                 // odd stride: conflict-free shared-memory lanes
+    // Split each row over wpr warps so that a lane holds at most kIirLmax samples; the
+    // per-lane length L is odd (conflict-free strided shared-memory access).
+    int wpr = 1;
+    while (32 * wpr * fbp::kIirLmax < p->M) ++wpr;
+    int L = (p->M + 32 * wpr - 1) / (32 * wpr);
+    if ((L & 1) == 0) ++L;
     prm.L = L;
+    prm.wpr = wpr;
 
     int q = p->coeffs.q;
-    const int mb = p->coeffs.mb;
+    const int mb0 = p->coeffs.mb;
     while (q > 0 && p->coeffs.a[q - 1] == 0.0) --q;       // trailing zero coefficients
     const double* a = p->coeffs.a;
     const double* b = p->coeffs.b;
 
+    // A DC-free numerator (B(1) = 0, as for the fitted ramp filters) factors as
+    // B(w) = (1 - w) B'(w); the kernel then drives the modes with the first difference of
+    // the input and realises B'/A.  Otherwise B/A is realised on the input itself.
+    double bsum = 0.0, babs = 0.0;
+    for (int k = 0; k < mb0; ++k) { bsum += b[k]; babs += fabs(b[k]); }
+    std::vector<double> num(b, b + mb0);
+    prm.diff = 0;
+    if (mb0 >= 2 && fabs(bsum) <= 1e-12 * babs) {
+        prm.diff = 1;
+        num.assign(mb0 - 1, 0.0);
+        double acc = 0.0;
+        for (int k = 0; k < mb0 - 1; ++k) { acc += b[k]; num[k] = acc; }
+    }
+    const int mb = (int)num.size();
+
     // polynomial part and proper remainder (long division in powers of w)
-    std::vector<double> rem(b, b + mb), D;
+    std::vector<double> rem(num), D;
     if (mb - 1 >= q) {
         if (q == 0) {
             D = rem;
@@ -179,17 +199,20 @@ fbp_status build_iir_params(fbp_plan_s* p)
         std::vector<double> h(T, 0.0);
         double scale = 0.0;
         for (int n = 0; n < T; ++n) {
-            double v = n < mb ? b[n] : 0.0;
+            double v = n < mb0 ? b[n] : 0.0;
             for (int k = 1; k <= q; ++k)
                 if (n - k >= 0) v -= a[k - 1] * h[n - k];
             h[n] = v;
             scale = fmax(scale, fabs(v));
         }
         double err = 0.0;
+        double gprev = 0.0;
         for (int n = 0; n < T; ++n) {
             cplx g = n < prm.nd ? D[n] : 0.0;
             for (int j = 0; j < q; ++j) g += res[j] * std::pow(pole[j], n);
-            err = fmax(err, fabs(g.real() - h[n]));
+            const double gn = g.real();
+            err = fmax(err, fabs((prm.diff ? gn - gprev : gn) - h[n]));
+            gprev = gn;
         }
         if (!(err <= 1e-9 * fmax(scale, 1e-300))) return FBP_ERR_UNSUPPORTED;
     }
@@ -205,6 +228,7 @@ fbp_status build_iir_params(fbp_plan_s* p)
             prm.rr[m] = (float)res[j].real();
             double c = carry.real();
             for (int d = 0; d < fbp::kScanSteps; ++d, c *= c) prm.rpow[d][m] = (float)c;
+            prm.rwarp[m] = (float)std::pow(pj, 32 * L).real();
         } else if (pj.imag() > 0.0) {
             const int m = prm.jc++;
             prm.cpr[m] = (float)pj.real();
@@ -215,6 +239,9 @@ fbp_status build_iir_params(fbp_plan_s* p)
                 prm.cpowr[d][m] = (float)carry.real();
                 prm.cpowi[d][m] = (float)carry.imag();
             }
+            const cplx pw = std::pow(pj, 32 * L);
+            prm.cwarpr[m] = (float)pw.real();
+            prm.cwarpi[m] = (float)pw.imag();
         }
     }
     if (prm.jr + 2 * prm.jc != q) return FBP_ERR_UNSUPPORTED;     // unpaired complex root
@@ -348,7 +375,7 @@ cudaError_t reconstruct_chunk(fbp_plan_s* p, const float* sino, float* img, int 
     float* filt = ws_ptr(p, p->off_filt);
     float* g = ws_ptr(p, p->off_g);
     cudaError_t e = run(p, FBP_KERNEL_IIR, st,
-                        [&] { return fbp::launch_iir(p, sino, filt, cnt * p->K, st); });
+                        [&] { return fbp::launch_iir(p, sino, filt, cnt * p->K, fbp::filt_pitch(p), st); });
     if (e == cudaSuccess)
         e = run(p, FBP_KERNEL_PASS1_RESAMPLE, st,
                 [&] { return fbp::launch_pass1(p, filt, false, g, cnt, st); });
@@ -403,7 +430,8 @@ fbp_status fbp_plan(fbp_plan_t* out, int N, int K, int M, int batch,
     if (!out) return FBP_ERR_INVALID_ARG;
     *out = nullptr;
     if (N < 2 || N > 4096 || (N & (N - 1)) != 0) return FBP_ERR_UNSUPPORTED;
-    if (K < 2 || M < 2 || M > 28000 || batch < 1) return FBP_ERR_INVALID_ARG;
+    if (K < 2 || M < 2 || M > 32 * fbp::kIirMaxWarps * fbp::kIirLmax || batch < 1)
+        return FBP_ERR_INVALID_ARG;
     fbp_iir_coeffs c;
     if (coeffs) {
         c = *coeffs;
@@ -445,6 +473,7 @@ fbp_status fbp_plan(fbp_plan_t* out, int N, int K, int M, int batch,
     if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return FBP_ERR_CUDA; }
 
     const size_t s_bytes = fbp::sino_floats(p) * sizeof(float);
+    const size_t f_bytes = (size_t)K * fbp::filt_pitch(p) * sizeof(float);
     const size_t g_bytes = fbp::lin_floats(p) * sizeof(float);
     size_t chunk = kL2Budget / (s_bytes + g_bytes);
     if (chunk < 1) chunk = 1;
@@ -452,7 +481,7 @@ fbp_status fbp_plan(fbp_plan_t* out, int N, int K, int M, int batch,
     if (chunk > (size_t)batch) chunk = batch;
     p->chunk = (int)chunk;
     size_t off = 0;
-    p->off_filt = off; off = align_up(off + chunk * s_bytes);
+    p->off_filt = off; off = align_up(off + chunk * f_bytes);
     p->off_g = off; off = align_up(off + chunk * g_bytes);
     for (int b = 0; b < 2; ++b) { p->off_stage_sino[b] = off; off = align_up(off + chunk * s_bytes); }
     for (int b = 0; b < 2; ++b) {
@@ -569,7 +598,7 @@ fbp_status fbp_filter_iir(fbp_plan_t p, const float* d_sino, float* d_filt, void
     if (!g.ok) return FBP_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     return cuda_status(run(p, FBP_KERNEL_IIR, st, [&] {
-        return fbp::launch_iir(p, d_sino, d_filt, p->batch * p->K, st);
+        return fbp::launch_iir(p, d_sino, d_filt, p->batch * p->K, p->M, st);
     }));
 }
 

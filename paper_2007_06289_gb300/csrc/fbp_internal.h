@@ -35,14 +35,22 @@ struct RowGeom {
 //   s_j(n) = p_j s_j(n-1) + x(n).
 // jr real modes, jc complex modes (one per conjugate pair, residue doubled), nd direct taps.
 // pow*[d] = p^(L 2^d) carries a mode's state across 2^d lanes of L samples each.
+// A row is split over wpr warps (32 wpr lanes, L samples per lane): p^(32 L) carries a
+// mode's state across one warp.  With diff = 1 the modes are driven by the first
+// difference of the input (B(z) = (1 - z^-1) B'(z) when B(1) = 0): DC-free filters then
+// need no cancellation between large mode outputs.
 struct IirParams {
-    int jr, jc, nd, L;
+    int jr, jc, nd, L, wpr, diff;
     float rp[kMaxOrder], rr[kMaxOrder];
     float cpr[kMaxOrder / 2], cpi[kMaxOrder / 2], crr[kMaxOrder / 2], cri[kMaxOrder / 2];
     float rpow[kScanSteps][kMaxOrder];
     float cpowr[kScanSteps][kMaxOrder / 2], cpowi[kScanSteps][kMaxOrder / 2];
+    float rwarp[kMaxOrder];
+    float cwarpr[kMaxOrder / 2], cwarpi[kMaxOrder / 2];
     float d[kMaxOrder];
 };
+constexpr int kIirLmax = 23;       // samples per lane (odd: conflict-free strided access)
+constexpr int kIirMaxWarps = 32;   // warps per row, so M <= 32 * 32 * 23
 
 }  // namespace fbp
 
@@ -76,8 +84,10 @@ struct fbp_plan_s {
 namespace fbp {
 
 // Kernel launchers (each returns cudaGetLastError() after the launch).
+// out_pitch >= M: output rows are out_pitch floats apart, the M samples centred in each
+// with (out_pitch - M) / 2 zeros before them and the rest after (guard bins).
 cudaError_t launch_iir(const fbp_plan_s* p, const float* in, float* out, int rows,
-                       cudaStream_t st);
+                       int out_pitch, cudaStream_t st);
 cudaError_t launch_resample(const fbp_plan_s* p, const float* filt, float* lin, int count,
                             cudaStream_t st);
 cudaError_t launch_pass1(const fbp_plan_s* p, const float* src, bool from_lin, float* g,
@@ -90,6 +100,11 @@ cudaError_t launch_fir(const fbp_plan_s* p, const float* in, float* out, int row
                        cudaStream_t st);
 cudaError_t launch_direct_bp(const fbp_plan_s* p, const float* filt, float* img, int count,
                              cudaStream_t st);
+
+// The fused pipeline keeps its filtered sinogram with kGuard zero bins on both sides of
+// every row, so resampling reads bins -kGuard .. M+kGuard-1 without range checks.
+constexpr int kGuard = 2;
+inline int filt_pitch(const fbp_plan_s* p) { return p->M + 2 * kGuard; }
 
 inline size_t lin_floats(const fbp_plan_s* p) { return (size_t)4 * p->N * 2 * p->N; }
 inline size_t sino_floats(const fbp_plan_s* p) { return (size_t)p->K * p->M; }

@@ -314,10 +314,11 @@ struct GSink {
 };
 
 struct Pass1Args {
-    const float* src;       // filtered sinogram [count][K][M] or linogram [count][4][N][2N]
+    const float* src;       // filtered sinogram [count][K][pitch] (guarded rows) or
+                            // linogram [count][4][N][2N]
     float* g;               // [count][4][N][2N]
     const RowGeom* geom;
-    int N, K, M;
+    int N, K, M, pitch;
 };
 
 // CTA = (column tile, quarter * blocks + block, slice).  Resamples (or loads) the block's
@@ -356,8 +357,11 @@ pass1_kernel(Pass1Args a)
         // One warp per linogram row, lane = column within each 32-column group.  Each batch
         // of kS samples issues all of its gathers before combining any of them; the
         // arithmetic is the same as linogram_sample's, term for term.
-        const float* pt = a.src + (size_t)s * a.K * a.M;
+        // rows of the filtered sinogram are `pitch` floats apart with kGuard zero bins on
+        // each side; pt points at bin 0 of row 0 of this slice
+        const float* pt = a.src + (size_t)s * a.K * a.pitch + kGuard;
         const int M = a.M;
+        const int pitch = a.pitch;
         constexpr int kS = 4;
         for (int j = warp; j < R; j += NWARPS) {
             const int i = bi * R + j;
@@ -369,38 +373,32 @@ pass1_kernel(Pass1Args a)
                 continue;
             }
             const RowGeom gm = a.geom[q * N + i];
-            const float* ra = pt + (size_t)gm.k0 * M;
+            const float* ra = pt + (size_t)gm.k0 * pitch;
             const long long m0 = gm.b_fx + gm.a_fx * (long long)(c0 + lane);
             const long long step = gm.a_fx * 32;
             if (!gm.wrap) {
-                // Angle rows k0 and k0+1 are adjacent: one clamped address serves all four
-                // bins; the selects restore the zero padding outside [0, M).
+                // Angle rows k0 and k0+1 are adjacent.  Clamping the bin to [-kGuard, M]
+                // keeps bins j and j+1 inside the guarded row, and a clamped bin only
+                // happens when both true bins lie outside [0, M), where the guards read 0:
+                // the result equals zero padding without any select.
                 long long m = m0;
 #pragma unroll
                 for (int kb = 0; kb < WB / 32; kb += kS) {
                     float l0[kS], l1[kS], l2[kS], l3[kS], fr[kS];
-                    int dd[kS];
 #pragma unroll
                     for (int k = 0; k < kS; ++k, m += step) {
                         int j;
                         split_fixed(m, j, fr[k]);
-                        const int jc = min(max(j, 0), M - 2);
-                        dd[k] = j - jc;
-                        const float* pp = ra + jc;
+                        const float* pp = ra + min(max(j, -kGuard), M);
                         l0[k] = __ldg(pp);
                         l1[k] = __ldg(pp + 1);
-                        l2[k] = __ldg(pp + M);
-                        l3[k] = __ldg(pp + M + 1);
+                        l2[k] = __ldg(pp + pitch);
+                        l3[k] = __ldg(pp + pitch + 1);
                     }
 #pragma unroll
                     for (int k = 0; k < kS; ++k) {
-                        const int d = dd[k];
-                        const float a0 = d == 0 ? l0[k] : (d == 1 ? l1[k] : 0.0f);
-                        const float a1 = d == 0 ? l1[k] : (d == -1 ? l0[k] : 0.0f);
-                        const float b0 = d == 0 ? l2[k] : (d == 1 ? l3[k] : 0.0f);
-                        const float b1 = d == 0 ? l3[k] : (d == -1 ? l2[k] : 0.0f);
-                        const float va = fmaf(fr[k], a1 - a0, a0);
-                        const float vb = fmaf(fr[k], b1 - b0, b0);
+                        const float va = fmaf(fr[k], l1[k] - l0[k], l0[k]);
+                        const float vb = fmaf(fr[k], l3[k] - l2[k], l2[k]);
                         const float v = gm.w * fmaf(gm.ft, vb - va, va);
                         row[33 * (kb + k)] = (c0 + lane + 32 * (kb + k) <= limit) ? v : 0.0f;
                     }
@@ -570,7 +568,7 @@ cudaError_t launch_pass1_t(const fbp_plan_s* p, const float* src, float* g, int 
     const int nblocks = p->N >> LOGR;
     const int max_cols = p->N + R * (nblocks - 1);
     dim3 grid((max_cols + T - 1) / T, 4 * nblocks, count);
-    Pass1Args a{src, g, p->d_geom, p->N, p->K, p->M};
+    Pass1Args a{src, g, p->d_geom, p->N, p->K, p->M, filt_pitch(p)};
     pass1_kernel<LOGR, FROM_LIN><<<grid, kNT1, pass1_smem<LOGR>(), st>>>(a);
     return cudaGetLastError();
 }

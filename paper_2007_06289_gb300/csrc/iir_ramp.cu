@@ -8,17 +8,16 @@
 //   y(n) = sum_j Re(r_j s_j(n)) + sum_k d_k p(n-k),   s_j(n) = p_j s_j(n-1) + p(n),
 // which stays accurate in float32 where the direct form does not (its poles crowd z = 1).
 //
-// One warp filters one row.  The row is staged in shared memory with coalesced loads;
-// lane j owns the contiguous chunk [jL, jL+L) (L odd, so the lanes' strided shared-memory
-// accesses fall in 32 distinct banks).  Each mode is a first-order linear recurrence, so
-// each direction runs as a blocked scan:
-//   1. every lane runs its chunk from zero state and keeps the end state e_j;
-//   2. a Kogge-Stone scan over the 32 lanes composes S_{j+1} = p^L S_j + e_j with the
-//      host-precomputed powers p^(L 2^d);
-//   3. every lane reruns its chunk from its true incoming state and emits the output.
-// The causal result is parked in a second shared buffer, the anticausal result is added
-// to it, and the row is written back with coalesced stores: one HBM read and one HBM
-// write per sample for both directions.
+// A row is filtered by wpr warps: it is staged once in shared memory (asynchronous
+// coalesced copies) and lane l of warp w owns the chunk of L consecutive samples starting
+// at (32 w + l) L (L odd, at most kIirLmax, so the lanes' strided reads fall in distinct
+// banks).  Each mode is a first-order linear recurrence, so each direction is a blocked
+// scan: every lane runs its chunk from zero state; the end states are combined by a
+// Kogge-Stone scan across the warp (powers p^(L 2^d)) and a Horner sweep across the warps
+// of the row (power p^(32 L), warp totals exchanged in shared memory); every lane then
+// reruns its chunk from its true incoming state.  The anticausal result of a lane stays in
+// registers until the causal pass adds to it; the sum overwrites the staged row in place
+// and is written back with coalesced stores: one HBM read and one write per sample.
 #include "fbp_internal.h"
 
 namespace fbp {
@@ -26,6 +25,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxSmem = 227 * 1024;     // shared memory per CTA on sm_103a
+constexpr int kIirThreads = 256;
 
 template <int JR, int JC>
 struct ModeState {
@@ -70,166 +70,274 @@ __device__ __forceinline__ float output(const ModeState<JR, JC>& s, const IirPar
     return y;
 }
 
+// s <- m s + u, mode by mode, for per-mode multipliers m given as real / complex arrays
+template <int JR, int JC>
+__device__ __forceinline__ void mul_add(ModeState<JR, JC>& s, const float* mr, const float* mcr,
+                                        const float* mci, const ModeState<JR, JC>& u)
+{
+#pragma unroll
+    for (int j = 0; j < JR; ++j) s.r[j] = fmaf(mr[j], s.r[j], u.r[j]);
+#pragma unroll
+    for (int j = 0; j < JC; ++j) {
+        const float nr = fmaf(mcr[j], s.cr[j], fmaf(-mci[j], s.ci[j], u.cr[j]));
+        const float ni = fmaf(mci[j], s.cr[j], fmaf(mcr[j], s.ci[j], u.ci[j]));
+        s.cr[j] = nr;
+        s.ci[j] = ni;
+    }
+}
+
 template <bool FORWARD>
 __device__ __forceinline__ float shfl(float v, int off)
 {
     return FORWARD ? __shfl_up_sync(kFull, v, off) : __shfl_down_sync(kFull, v, off);
 }
 
-// Exclusive scan of the lanes' end states: on return s holds the state entering this
-// lane's chunk (from lower lanes if FORWARD, from higher lanes otherwise).
 template <int JR, int JC, bool FORWARD>
-__device__ __forceinline__ void carry_scan(ModeState<JR, JC>& s, const IirParams& prm, int lane)
+__device__ __forceinline__ ModeState<JR, JC> shfl_state(const ModeState<JR, JC>& s, int off)
+{
+    ModeState<JR, JC> u;
+#pragma unroll
+    for (int j = 0; j < JR; ++j) u.r[j] = shfl<FORWARD>(s.r[j], off);
+#pragma unroll
+    for (int j = 0; j < JC; ++j) {
+        u.cr[j] = shfl<FORWARD>(s.cr[j], off);
+        u.ci[j] = shfl<FORWARD>(s.ci[j], off);
+    }
+    return u;
+}
+
+// Inclusive Kogge-Stone scan of the lanes' end states within a warp (towards higher lanes
+// if FORWARD): afterwards lane l holds the state after its own chunk given zero state at
+// the warp's first chunk.
+template <int JR, int JC, bool FORWARD>
+__device__ __forceinline__ void warp_scan(ModeState<JR, JC>& s, const IirParams& prm, int lane)
 {
 #pragma unroll
     for (int d = 0; d < kScanSteps; ++d) {
         const int off = 1 << d;
-        const bool take = FORWARD ? (lane >= off) : (lane + off < 32);
+        const ModeState<JR, JC> u = shfl_state<JR, JC, FORWARD>(s, off);
+        if (FORWARD ? (lane >= off) : (lane + off < 32)) {
+            ModeState<JR, JC> t = u;
+            // s <- p^(L 2^d) u + s
 #pragma unroll
-        for (int j = 0; j < JR; ++j) {
-            const float u = shfl<FORWARD>(s.r[j], off);
-            if (take) s.r[j] = fmaf(prm.rpow[d][j], u, s.r[j]);
-        }
+            for (int j = 0; j < JR; ++j) t.r[j] = fmaf(prm.rpow[d][j], u.r[j], s.r[j]);
 #pragma unroll
-        for (int j = 0; j < JC; ++j) {
-            const float ur = shfl<FORWARD>(s.cr[j], off);
-            const float ui = shfl<FORWARD>(s.ci[j], off);
-            if (take) {
+            for (int j = 0; j < JC; ++j) {
                 const float pr = prm.cpowr[d][j], pi = prm.cpowi[d][j];
-                s.cr[j] = fmaf(pr, ur, fmaf(-pi, ui, s.cr[j]));
-                s.ci[j] = fmaf(pi, ur, fmaf(pr, ui, s.ci[j]));
+                t.cr[j] = fmaf(pr, u.cr[j], fmaf(-pi, u.ci[j], s.cr[j]));
+                t.ci[j] = fmaf(pi, u.cr[j], fmaf(pr, u.ci[j], s.ci[j]));
+            }
+            s = t;
+        }
+    }
+}
+
+// p^(L k) for 0 <= k < 32, from the binary powers p^(L 2^d)
+template <int JR, int JC>
+__device__ __forceinline__ void lane_power(float* mr, float* mcr, float* mci, const IirParams& prm,
+                                           int k)
+{
+#pragma unroll
+    for (int j = 0; j < JR; ++j) mr[j] = 1.0f;
+#pragma unroll
+    for (int j = 0; j < JC; ++j) { mcr[j] = 1.0f; mci[j] = 0.0f; }
+#pragma unroll
+    for (int d = 0; d < kScanSteps; ++d) {
+        if ((k >> d) & 1) {
+#pragma unroll
+            for (int j = 0; j < JR; ++j) mr[j] *= prm.rpow[d][j];
+#pragma unroll
+            for (int j = 0; j < JC; ++j) {
+                const float pr = prm.cpowr[d][j], pi = prm.cpowi[d][j];
+                const float nr = mcr[j] * pr - mci[j] * pi;
+                mci[j] = mcr[j] * pi + mci[j] * pr;
+                mcr[j] = nr;
             }
         }
-    }
-    const bool edge = FORWARD ? (lane == 0) : (lane == 31);
-#pragma unroll
-    for (int j = 0; j < JR; ++j) {
-        const float u = shfl<FORWARD>(s.r[j], 1);
-        s.r[j] = edge ? 0.0f : u;
-    }
-#pragma unroll
-    for (int j = 0; j < JC; ++j) {
-        const float ur = shfl<FORWARD>(s.cr[j], 1);
-        const float ui = shfl<FORWARD>(s.ci[j], 1);
-        s.cr[j] = edge ? 0.0f : ur;
-        s.ci[j] = edge ? 0.0f : ui;
     }
 }
 
 template <int JR, int JC>
-__global__ void __launch_bounds__(128)
-iir_ramp_kernel(const float* in, float* out, int rows, int M, int warps_per_cta, IirParams prm)
+constexpr int state_floats() { return JR + 2 * JC > 0 ? JR + 2 * JC : 1; }
+
+template <int JR, int JC>
+__device__ __forceinline__ void put_state(float* dst, const ModeState<JR, JC>& s)
 {
+#pragma unroll
+    for (int j = 0; j < JR; ++j) dst[j] = s.r[j];
+#pragma unroll
+    for (int j = 0; j < JC; ++j) { dst[JR + 2 * j] = s.cr[j]; dst[JR + 2 * j + 1] = s.ci[j]; }
+}
+
+template <int JR, int JC>
+__device__ __forceinline__ ModeState<JR, JC> get_state(const float* src)
+{
+    ModeState<JR, JC> s;
+#pragma unroll
+    for (int j = 0; j < JR; ++j) s.r[j] = src[j];
+#pragma unroll
+    for (int j = 0; j < JC; ++j) { s.cr[j] = src[JR + 2 * j]; s.ci[j] = src[JR + 2 * j + 1]; }
+    return s;
+}
+
+// One direction of the blocked scan.  On return s holds the state entering this lane's
+// chunk.  `tot` is this row's [wpr] array of warp totals for this direction.
+template <int JR, int JC, bool FORWARD>
+__device__ __forceinline__ void incoming_state(ModeState<JR, JC>& s, const IirParams& prm,
+                                               float* tot, int w, int lane)
+{
+    constexpr int SF = state_floats<JR, JC>();
+    const int wpr = prm.wpr;
+    warp_scan<JR, JC, FORWARD>(s, prm, lane);
+    if (lane == (FORWARD ? 31 : 0)) put_state(tot + w * SF, s);
+    __syncthreads();
+    // carry from the preceding warps of the row (in scan direction), by Horner's rule
+    ModeState<JR, JC> c;
+    zero_state(c);
+    if (FORWARD) {
+        for (int v = 0; v < w; ++v) mul_add(c, prm.rwarp, prm.cwarpr, prm.cwarpi, get_state<JR, JC>(tot + v * SF));
+    } else {
+        for (int v = wpr - 1; v > w; --v) mul_add(c, prm.rwarp, prm.cwarpr, prm.cwarpi, get_state<JR, JC>(tot + v * SF));
+    }
+    // exclusive within the warp, plus the warp carry brought through the earlier lanes
+    ModeState<JR, JC> e = shfl_state<JR, JC, FORWARD>(s, 1);
+    if (lane == (FORWARD ? 0 : 31)) zero_state(e);
+    float mr[JR > 0 ? JR : 1], mcr[JC > 0 ? JC : 1], mci[JC > 0 ? JC : 1];
+    lane_power<JR, JC>(mr, mcr, mci, prm, FORWARD ? lane : 31 - lane);
+    s = e;
+    // s = p^(L k) c + e
+    ModeState<JR, JC> t = c;
+    mul_add(t, mr, mcr, mci, e);
+    s = t;
+}
+
+template <int JR, int JC>
+__global__ void __launch_bounds__(kIirThreads)
+iir_ramp_kernel(const float* in, float* out, int rows, int M, int out_pitch, int rows_per_cta,
+                IirParams prm)
+{
+    constexpr int SF = state_floats<JR, JC>();
     extern __shared__ float smem[];
+    const int wpr = prm.wpr;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const long long row = (long long)blockIdx.x * warps_per_cta + warp;
-    if (warp >= warps_per_cta || row >= rows) return;     // whole warps leave together
+    const int rloc = warp / wpr;
+    const int w = warp - rloc * wpr;
+    const long long row = (long long)blockIdx.x * rows_per_cta + rloc;
+    const bool live = rloc < rows_per_cta && row < rows;
+    // idle warps still take part in the block-wide barriers below
+    float* sp = smem + (size_t)min(rloc, rows_per_cta - 1) * M;
+    float* tot = smem + (size_t)rows_per_cta * M + (size_t)min(rloc, rows_per_cta - 1) * 2 * wpr * SF;
 
-    float* sp = smem + (size_t)warp * 2 * M;              // input row
-    float* sy = sp + M;                                    // result row
-    const float* src = in + row * (long long)M;
-    // every element of the row in flight at once: asynchronous 4-byte copies into shared
-    for (int n = lane; n < M; n += 32) {
-        const unsigned d = (unsigned)__cvta_generic_to_shared(sp + n);
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src + n) : "memory");
+    if (live) {
+        const float* src = in + row * (long long)M;
+        for (int n = w * 32 + lane; n < M; n += 32 * wpr) {
+            const unsigned d = (unsigned)__cvta_generic_to_shared(sp + n);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src + n) : "memory");
+        }
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
-    __syncwarp();
+    __syncthreads();
 
     const int L = prm.L;
-    const int n0 = min(lane * L, M);
-    const int n1 = min(n0 + L, M);
+    const int n0 = live ? min((w * 32 + lane) * L, M) : M;
+    const int len = min(n0 + L, M) - n0;
     const int nd = prm.nd;
+    // Mode input: x(n) - x(n-1) causally and x(n) - x(n+1) anticausally when the plan
+    // factored (1 - z^-1) out of the numerator, else x(n); x = 0 outside [0, M).
+    const float dmask = prm.diff ? 1.0f : 0.0f;
+    auto xs = [&](int m) { return (m >= 0 && m < M) ? sp[m] : 0.0f; };
+    const float right = len > 0 ? xs(n0 + len) : 0.0f;
+    const float left = len > 0 ? xs(n0 - 1) : 0.0f;
     ModeState<JR, JC> s;
-    // The recurrences read the chunk in blocks of kB samples fetched ahead into registers,
-    // so shared-memory latency stays off the dependency chain.
-    constexpr int kB = 8;
-    auto causal_out = [&](int n) {
-        float y = output(s, prm);
-        for (int k = 0; k < nd; ++k)
-            if (n - k >= 0) y = fmaf(prm.d[k], sp[n - k], y);
-        sy[n] = y;
-    };
-    auto anticausal_out = [&](int n) {
-        float z = output(s, prm);
-        for (int k = 0; k < nd; ++k)
-            if (n + k < M) z = fmaf(prm.d[k], sp[n + k], z);
-        sy[n] += z;
-    };
+    float acc[kIirLmax];          // anticausal output of this lane's chunk, then the sum
 
-    // causal: local pass from zero state, carry scan, final pass
+    // anticausal: local pass from zero state (right to left), scan, final pass
     zero_state(s);
-    int n = n0;
-    for (; n + kB <= n1; n += kB) {
-        float x[kB];
+    float nb = right;
 #pragma unroll
-        for (int k = 0; k < kB; ++k) x[k] = sp[n + k];
-#pragma unroll
-        for (int k = 0; k < kB; ++k) step(s, prm, x[k]);
-    }
-    for (; n < n1; ++n) step(s, prm, sp[n]);
-    carry_scan<JR, JC, true>(s, prm, lane);
-    n = n0;
-    for (; n + kB <= n1; n += kB) {
-        float x[kB];
-#pragma unroll
-        for (int k = 0; k < kB; ++k) x[k] = sp[n + k];
-#pragma unroll
-        for (int k = 0; k < kB; ++k) {
-            step(s, prm, x[k]);
-            causal_out(n + k);
+    for (int k = kIirLmax - 1; k >= 0; --k) {
+        if (k < len) {
+            const float xv = sp[n0 + k];
+            step(s, prm, fmaf(-dmask, nb, xv));
+            nb = xv;
         }
     }
-    for (; n < n1; ++n) {
-        step(s, prm, sp[n]);
-        causal_out(n);
-    }
-
-    // anticausal: the same, walking the chunk backwards
-    zero_state(s);
-    n = n1 - 1;
-    for (; n - kB + 1 >= n0; n -= kB) {
-        float x[kB];
+    incoming_state<JR, JC, false>(s, prm, tot + wpr * SF, w, lane);
+    nb = right;
 #pragma unroll
-        for (int k = 0; k < kB; ++k) x[k] = sp[n - k];
-#pragma unroll
-        for (int k = 0; k < kB; ++k) step(s, prm, x[k]);
-    }
-    for (; n >= n0; --n) step(s, prm, sp[n]);
-    carry_scan<JR, JC, false>(s, prm, lane);
-    n = n1 - 1;
-    for (; n - kB + 1 >= n0; n -= kB) {
-        float x[kB];
-#pragma unroll
-        for (int k = 0; k < kB; ++k) x[k] = sp[n - k];
-#pragma unroll
-        for (int k = 0; k < kB; ++k) {
-            step(s, prm, x[k]);
-            anticausal_out(n - k);
+    for (int k = kIirLmax - 1; k >= 0; --k) {
+        if (k < len) {
+            const float xv = sp[n0 + k];
+            step(s, prm, fmaf(-dmask, nb, xv));
+            nb = xv;
+            float z = output(s, prm);
+            for (int t = 0; t < nd; ++t) {
+                const int m = n0 + k + t;
+                z = fmaf(prm.d[t], fmaf(-dmask, xs(m + 1), xs(m)), z);
+            }
+            acc[k] = z;
         }
     }
-    for (; n >= n0; --n) {
-        step(s, prm, sp[n]);
-        anticausal_out(n);
-    }
-    __syncwarp();
 
-    float* dst = out + row * (long long)M;
-    for (int n = lane; n < M; n += 32) dst[n] = sy[n];
+    // causal: local pass, scan, final pass adding y to the anticausal z
+    zero_state(s);
+    float pb = left;
+#pragma unroll
+    for (int k = 0; k < kIirLmax; ++k) {
+        if (k < len) {
+            const float xv = sp[n0 + k];
+            step(s, prm, fmaf(-dmask, pb, xv));
+            pb = xv;
+        }
+    }
+    incoming_state<JR, JC, true>(s, prm, tot, w, lane);
+    pb = left;
+#pragma unroll
+    for (int k = 0; k < kIirLmax; ++k) {
+        if (k < len) {
+            const float xv = sp[n0 + k];
+            step(s, prm, fmaf(-dmask, pb, xv));
+            pb = xv;
+            float y = output(s, prm);
+            for (int t = 0; t < nd; ++t) {
+                const int m = n0 + k - t;
+                y = fmaf(prm.d[t], fmaf(-dmask, xs(m - 1), xs(m)), y);
+            }
+            acc[k] = y + acc[k];
+        }
+    }
+    __syncthreads();                                       // every lane done reading sp
+#pragma unroll
+    for (int k = 0; k < kIirLmax; ++k)
+        if (k < len) sp[n0 + k] = acc[k];
+    __syncthreads();
+
+    if (live) {
+        const int lead = (out_pitch - M) / 2;
+        float* dst = out + row * (long long)out_pitch;
+        if (w == 0) {
+            if (lane < lead) dst[lane] = 0.0f;
+            if (lane < out_pitch - M - lead) dst[lead + M + lane] = 0.0f;
+        }
+        dst += lead;
+        for (int n = w * 32 + lane; n < M; n += 32 * wpr) dst[n] = sp[n];
+    }
 }
 
 template <int JR, int JC>
 cudaError_t launch_iir_t(const fbp_plan_s* p, const float* in, float* out, int rows,
-                         cudaStream_t st)
+                         int out_pitch, cudaStream_t st)
 {
-    const size_t per_warp = (size_t)2 * p->M * sizeof(float);
-    int warps = (int)(kMaxSmem / per_warp);
-    warps = warps > 4 ? 4 : warps;
-    if (warps < 1) return cudaErrorInvalidValue;
-    const size_t smem = per_warp * warps;
-    const int grid = (rows + warps - 1) / warps;
-    iir_ramp_kernel<JR, JC><<<grid, 128, smem, st>>>(in, out, rows, p->M, warps, p->iir);
+    constexpr int SF = state_floats<JR, JC>();
+    const int wpr = p->iir.wpr;
+    const int rows_per_cta = wpr <= kIirThreads / 32 ? kIirThreads / 32 / wpr : 1;
+    const int threads = 32 * wpr * rows_per_cta;
+    const size_t smem = ((size_t)rows_per_cta * p->M + (size_t)rows_per_cta * 2 * wpr * SF) * sizeof(float);
+    if (smem > (size_t)kMaxSmem || threads > 1024) return cudaErrorInvalidValue;
+    const int grid = (rows + rows_per_cta - 1) / rows_per_cta;
+    iir_ramp_kernel<JR, JC><<<grid, threads, smem, st>>>(in, out, rows, p->M, out_pitch,
+                                                         rows_per_cta, p->iir);
     return cudaGetLastError();
 }
 
@@ -260,12 +368,12 @@ cudaError_t prepare_iir_kernels()
 }
 
 cudaError_t launch_iir(const fbp_plan_s* p, const float* in, float* out, int rows,
-                       cudaStream_t st)
+                       int out_pitch, cudaStream_t st)
 {
     if (rows <= 0) return cudaSuccess;
     const int jr = p->iir.jr, jc = p->iir.jc;
 #define FBP_X(R, C) \
-    if (jr == R && jc == C) return launch_iir_t<R, C>(p, in, out, rows, st);
+    if (jr == R && jc == C) return launch_iir_t<R, C>(p, in, out, rows, out_pitch, st);
     FBP_IIR_MODES(FBP_X)
 #undef FBP_X
     return cudaErrorInvalidValue;
