@@ -15,9 +15,10 @@
 // scan: every lane runs its chunk from zero state; the end states are combined by a
 // Kogge-Stone scan across the warp (powers p^(L 2^d)) and a Horner sweep across the warps
 // of the row (power p^(32 L), warp totals exchanged in shared memory); every lane then
-// reruns its chunk from its true incoming state.  The anticausal result of a lane stays in
-// registers until the causal pass adds to it; the sum overwrites the staged row in place
-// and is written back with coalesced stores: one HBM read and one write per sample.
+// reruns its chunk from its true incoming state.  The anticausal result goes to a second
+// shared row, the causal pass adds to it there, and the sum is written back with coalesced
+// stores: one HBM read and one write per sample.  Direct taps (absent from the fitted
+// filters) are a compile-time variant.
 #include "fbp_internal.h"
 
 namespace fbp {
@@ -211,7 +212,7 @@ __device__ __forceinline__ void incoming_state(ModeState<JR, JC>& s, const IirPa
     s = t;
 }
 
-template <int JR, int JC>
+template <int JR, int JC, bool TAPS>
 __global__ void __launch_bounds__(kIirThreads)
 iir_ramp_kernel(const float* in, float* out, int rows, int M, int out_pitch, int rows_per_cta,
                 IirParams prm)
@@ -225,9 +226,10 @@ iir_ramp_kernel(const float* in, float* out, int rows, int M, int out_pitch, int
     const int w = warp - rloc * wpr;
     const long long row = (long long)blockIdx.x * rows_per_cta + rloc;
     const bool live = rloc < rows_per_cta && row < rows;
-    // idle warps still take part in the block-wide barriers below
-    float* sp = smem + (size_t)min(rloc, rows_per_cta - 1) * M;
-    float* tot = smem + (size_t)rows_per_cta * M + (size_t)min(rloc, rows_per_cta - 1) * 2 * wpr * SF;
+    // per row: input samples sp[M], result sz[M]; then the warp totals of both directions
+    float* sp = smem + (size_t)rloc * 2 * M;
+    float* sz = sp + M;
+    float* tot = smem + (size_t)rows_per_cta * 2 * M + (size_t)rloc * 2 * wpr * SF;
 
     if (live) {
         const float* src = in + row * (long long)M;
@@ -241,76 +243,62 @@ iir_ramp_kernel(const float* in, float* out, int rows, int M, int out_pitch, int
 
     const int L = prm.L;
     const int n0 = live ? min((w * 32 + lane) * L, M) : M;
-    const int len = min(n0 + L, M) - n0;
-    const int nd = prm.nd;
+    const int n1 = min(n0 + L, M);
     // Mode input: x(n) - x(n-1) causally and x(n) - x(n+1) anticausally when the plan
     // factored (1 - z^-1) out of the numerator, else x(n); x = 0 outside [0, M).
     const float dmask = prm.diff ? 1.0f : 0.0f;
     auto xs = [&](int m) { return (m >= 0 && m < M) ? sp[m] : 0.0f; };
-    const float right = len > 0 ? xs(n0 + len) : 0.0f;
-    const float left = len > 0 ? xs(n0 - 1) : 0.0f;
+    const float right = xs(n1);
+    const float left = xs(n0 - 1);
     ModeState<JR, JC> s;
-    float acc[kIirLmax];          // anticausal output of this lane's chunk, then the sum
 
-    // anticausal: local pass from zero state (right to left), scan, final pass
+    // anticausal: local pass from zero state (right to left), scan, final pass into sz
     zero_state(s);
     float nb = right;
-#pragma unroll
-    for (int k = kIirLmax - 1; k >= 0; --k) {
-        if (k < len) {
-            const float xv = sp[n0 + k];
-            step(s, prm, fmaf(-dmask, nb, xv));
-            nb = xv;
-        }
+#pragma unroll 4
+    for (int n = n1 - 1; n >= n0; --n) {
+        const float xv = sp[n];
+        step(s, prm, fmaf(-dmask, nb, xv));
+        nb = xv;
     }
     incoming_state<JR, JC, false>(s, prm, tot + wpr * SF, w, lane);
     nb = right;
-#pragma unroll
-    for (int k = kIirLmax - 1; k >= 0; --k) {
-        if (k < len) {
-            const float xv = sp[n0 + k];
-            step(s, prm, fmaf(-dmask, nb, xv));
-            nb = xv;
-            float z = output(s, prm);
-            for (int t = 0; t < nd; ++t) {
-                const int m = n0 + k + t;
-                z = fmaf(prm.d[t], fmaf(-dmask, xs(m + 1), xs(m)), z);
-            }
-            acc[k] = z;
+#pragma unroll 4
+    for (int n = n1 - 1; n >= n0; --n) {
+        const float xv = sp[n];
+        step(s, prm, fmaf(-dmask, nb, xv));
+        nb = xv;
+        float z = output(s, prm);
+        if constexpr (TAPS) {
+            for (int t = 0; t < prm.nd; ++t)
+                z = fmaf(prm.d[t], fmaf(-dmask, xs(n + t + 1), xs(n + t)), z);
         }
+        sz[n] = z;
     }
 
     // causal: local pass, scan, final pass adding y to the anticausal z
     zero_state(s);
     float pb = left;
-#pragma unroll
-    for (int k = 0; k < kIirLmax; ++k) {
-        if (k < len) {
-            const float xv = sp[n0 + k];
-            step(s, prm, fmaf(-dmask, pb, xv));
-            pb = xv;
-        }
+#pragma unroll 4
+    for (int n = n0; n < n1; ++n) {
+        const float xv = sp[n];
+        step(s, prm, fmaf(-dmask, pb, xv));
+        pb = xv;
     }
     incoming_state<JR, JC, true>(s, prm, tot, w, lane);
     pb = left;
-#pragma unroll
-    for (int k = 0; k < kIirLmax; ++k) {
-        if (k < len) {
-            const float xv = sp[n0 + k];
-            step(s, prm, fmaf(-dmask, pb, xv));
-            pb = xv;
-            float y = output(s, prm);
-            for (int t = 0; t < nd; ++t) {
-                const int m = n0 + k - t;
-                y = fmaf(prm.d[t], fmaf(-dmask, xs(m - 1), xs(m)), y);
-            }
-            acc[k] = y + acc[k];
+#pragma unroll 4
+    for (int n = n0; n < n1; ++n) {
+        const float xv = sp[n];
+        step(s, prm, fmaf(-dmask, pb, xv));
+        pb = xv;
+        float y = output(s, prm);
+        if constexpr (TAPS) {
+            for (int t = 0; t < prm.nd; ++t)
+                y = fmaf(prm.d[t], fmaf(-dmask, xs(n - t - 1), xs(n - t)), y);
         }
+        sz[n] = y + sz[n];
     }
-    __syncthreads();                                       // every lane done reading sp
-#pragma unroll
-    for (int k = 0; k < kIirLmax; ++k)
-        if (k < len) sp[n0 + k] = acc[k];
     __syncthreads();
 
     if (live) {
@@ -321,11 +309,11 @@ iir_ramp_kernel(const float* in, float* out, int rows, int M, int out_pitch, int
             if (lane < out_pitch - M - lead) dst[lead + M + lane] = 0.0f;
         }
         dst += lead;
-        for (int n = w * 32 + lane; n < M; n += 32 * wpr) dst[n] = sp[n];
+        for (int n = w * 32 + lane; n < M; n += 32 * wpr) dst[n] = sz[n];
     }
 }
 
-template <int JR, int JC>
+template <int JR, int JC, bool TAPS>
 cudaError_t launch_iir_t(const fbp_plan_s* p, const float* in, float* out, int rows,
                          int out_pitch, cudaStream_t st)
 {
@@ -333,19 +321,23 @@ cudaError_t launch_iir_t(const fbp_plan_s* p, const float* in, float* out, int r
     const int wpr = p->iir.wpr;
     const int rows_per_cta = wpr <= kIirThreads / 32 ? kIirThreads / 32 / wpr : 1;
     const int threads = 32 * wpr * rows_per_cta;
-    const size_t smem = ((size_t)rows_per_cta * p->M + (size_t)rows_per_cta * 2 * wpr * SF) * sizeof(float);
+    const size_t smem = ((size_t)rows_per_cta * 2 * p->M + (size_t)rows_per_cta * 2 * wpr * SF) * sizeof(float);
     if (smem > (size_t)kMaxSmem || threads > 1024) return cudaErrorInvalidValue;
     const int grid = (rows + rows_per_cta - 1) / rows_per_cta;
-    iir_ramp_kernel<JR, JC><<<grid, threads, smem, st>>>(in, out, rows, p->M, out_pitch,
-                                                         rows_per_cta, p->iir);
+    iir_ramp_kernel<JR, JC, TAPS><<<grid, threads, smem, st>>>(in, out, rows, p->M, out_pitch,
+                                                               rows_per_cta, p->iir);
     return cudaGetLastError();
 }
 
 template <int JR, int JC>
 cudaError_t set_attr()
 {
-    return cudaFuncSetAttribute(iir_ramp_kernel<JR, JC>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaError_t e = cudaFuncSetAttribute(iir_ramp_kernel<JR, JC, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(iir_ramp_kernel<JR, JC, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    return e;
 }
 
 // Every (real modes, complex modes) split with jr + 2 jc <= 8.
@@ -372,8 +364,10 @@ cudaError_t launch_iir(const fbp_plan_s* p, const float* in, float* out, int row
 {
     if (rows <= 0) return cudaSuccess;
     const int jr = p->iir.jr, jc = p->iir.jc;
-#define FBP_X(R, C) \
-    if (jr == R && jc == C) return launch_iir_t<R, C>(p, in, out, rows, out_pitch, st);
+#define FBP_X(R, C)                                                                   \
+    if (jr == R && jc == C)                                                           \
+        return p->iir.nd > 0 ? launch_iir_t<R, C, true>(p, in, out, rows, out_pitch, st)  \
+                             : launch_iir_t<R, C, false>(p, in, out, rows, out_pitch, st);
     FBP_IIR_MODES(FBP_X)
 #undef FBP_X
     return cudaErrorInvalidValue;
