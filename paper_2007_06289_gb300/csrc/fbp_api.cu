@@ -129,6 +129,9 @@ fbp_status build_iir_params(fbp_plan_s* p)
     while (32 * wpr * fbp::kIirLmax < p->M) ++wpr;
     int L = (p->M + 32 * wpr - 1) / (32 * wpr);
     if ((L & 1) == 0) ++L;
+    // The kernel has a fully unrolled variant for L = kIirLmax: take it when the lanes it
+    // leaves idle (filtering zero padding) cost at most an eighth of the row.
+    if ((long long)(32 * wpr * fbp::kIirLmax - p->M) * 8 <= p->M) L = fbp::kIirLmax;
     prm.L = L;
     prm.wpr = wpr;
 
@@ -276,11 +279,12 @@ std::vector<fbp::RowGeom> build_geometry(int N, int K, int M)
             if (k0 > K - 1) k0 = K - 1;
             fbp::RowGeom& e = g[(size_t)q * N + i];
             e.k0 = (int)k0;
-            e.ft = (float)(tk - k0);
+            const double ft = tk - k0;
             e.wrap = (e.k0 + 1 >= K) ? 1 : 0;
             double w = (1.0 / (N - 1)) / (1.0 + s * s);
             if (i == 0 || i == N - 1) w *= 0.5;
-            e.w = (float)w;
+            e.w0 = (float)(w * (1.0 - ft));
+            e.w1 = (float)(w * ft);
             const double inv = 1.0 / sqrt(1.0 + s * s);
             double A = inv, B = -c0 * (1.0 + s) * inv;
             if (q == 3) { A = -A; B = -B; }

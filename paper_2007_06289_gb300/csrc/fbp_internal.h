@@ -16,16 +16,18 @@ constexpr int kScanSteps = 5;            // log2(32 lanes)
 
 // Per linogram row (quarter q, slope row i): where the row samples the filtered sinogram.
 // Detector index m(c) = A*c + B for stored column c, carried in signed 64-bit fixed point
-// with kFixBits fractional bits: stepping c by one adds a_fx exactly, and the fraction of m
-// comes out with ~2^-24 absolute accuracy at |m| ~ 4096.  Angle index k0 + ft; the second
-// angle row is k0+1, or row 0 with the detector mirrored (m -> M-1-m) when k0+1 == K
-// ("wrap", p(theta+pi, r) = p(theta, -r)).
-constexpr int kFixBits = 40;
+// with kFixBits = 32 fractional bits: stepping c by one adds a_fx exactly, the bin is the
+// high word and the fraction the low word (rounded to float: ~2^-25 absolute accuracy).
+// Angle index k0 + ft; the second angle row is k0+1, or row 0 with the detector mirrored
+// (m -> M-1-m) when k0+1 == K ("wrap", p(theta+pi, r) = p(theta, -r)).  The row weight w
+// (trapezoid in sigma, Jacobian 1/k_t^2) is folded into the angle interpolation weights:
+// sample = w1 * p(k0+1, m) + w0 * p(k0, m), w0 = w (1 - ft), w1 = w ft.
+constexpr int kFixBits = 32;
 struct RowGeom {
     int k0;
     int wrap;
-    float ft;
-    float w;        // row weight (trapezoid in sigma, Jacobian 1/k_t^2)
+    float w0;
+    float w1;
     long long a_fx;
     long long b_fx;
 };

@@ -44,10 +44,6 @@ __device__ __forceinline__ int rev_bits(int v, int bits)
     return bits == 0 ? 0 : (int)(__brev((unsigned)v) >> (32 - bits));
 }
 
-// Shared-memory column index with one pad word per 32 columns: a warp whose lanes hold
-// four consecutive columns each reads 32 distinct banks.
-__host__ __device__ constexpr int phys(int x) { return x + (x >> 5); }
-
 // Asynchronous 4-byte global -> shared copy; an invalid source writes 0.
 __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid)
 {
@@ -63,12 +59,13 @@ __device__ __forceinline__ void cp_async_wait_all()
 }
 
 // ------------------------------------------------------------------------ resampling
-// Detector position in fixed point -> integer bin j and fraction f in [0, 1).
+// Detector position in fixed point -> integer bin j (the high word) and fraction f in
+// [0, 1] (the low word, rounded to float; f = 1 stands for a position within 2^-25 of j+1).
+static_assert(kFixBits == 32, "bin and fraction are the two words of the position");
 __device__ __forceinline__ void split_fixed(long long m, int& j, float& f)
 {
-    j = (int)(m >> kFixBits);
-    const unsigned frac24 = (unsigned)(m >> (kFixBits - 24)) & 0xFFFFFFu;
-    f = (float)frac24 * (1.0f / 16777216.0f);
+    j = (int)(m >> 32);
+    f = __uint2float_rn((unsigned)m) * 0x1p-32f;
 }
 
 // Detector sample j of a row, zero outside [0, M); the load itself is never predicated
@@ -87,7 +84,8 @@ __device__ __forceinline__ float row_lerp(const float* __restrict__ row, int M, 
     return fmaf(f, v1 - v0, v0);
 }
 
-// One linogram sample at fixed-point detector position m: w * bilinear(p~, k0 + ft, m).
+// One linogram sample at fixed-point detector position m: w * bilinear(p~, k0 + ft, m),
+// with the weight folded into the angle interpolation.
 __device__ __forceinline__ float linogram_sample(const RowGeom& g, const float* __restrict__ pt,
                                                  int M, long long m)
 {
@@ -106,7 +104,7 @@ __device__ __forceinline__ float linogram_sample(const RowGeom& g, const float* 
         split_fixed(((long long)(M - 1) << kFixBits) - m, jm, fm);
         vb = row_lerp(pt, M, jm, fm);
     }
-    return g.w * fmaf(g.ft, vb - va, va);
+    return fmaf(g.w1, vb, g.w0 * va);
 }
 
 // Plain resampling into the stored linogram [count][4][N][2N] (every entry written).
@@ -125,54 +123,123 @@ resample_kernel(const float* __restrict__ filt, float* __restrict__ lin,
 }
 
 // ------------------------------------------------------------------------ Hough rounds
+// Hough rows live in shared memory unpadded, PITCH floats apart with PITCH a multiple of 4,
+// so column 4l of any row starts a 16-byte word.  Lane l of a warp owns columns 4l..4l+3 of
+// each 128-column chunk and moves them with 16-byte loads and stores: a warp's 16-byte
+// accesses cover 512 consecutive bytes, which the shared memory serves without bank
+// conflicts.  A shifted read (columns 4l + t + k) loads the aligned words around it and
+// picks the values in registers; the pick depends only on t mod 4, which is the same for the
+// whole warp, so each of the four cases is compiled separately.
+//
 // A round hands each thread's results -- four consecutive columns x0..x0+3 of one row --
 // to a sink.  SmemSink writes them back in place (every round but a pass's last); a pass
 // may give its last round a sink that stores straight to global memory.
 struct SmemSink {};
 
-template <int PITCH>
-__device__ __forceinline__ void smem_put(float* row, int p, const float (&o)[4])
+__device__ __forceinline__ void ld4(float* v, const float* p)
 {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) row[p + k] = o[k];
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+
+__device__ __forceinline__ void st4(float* p, const float (&o)[4])
+{
+    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
 }
 
 // Stage 1 (shift 0) on row pairs (2m, 2m+1), in place, one warp per pair.
 template <int R, int WB, int PITCH, int NWARPS, class Sink>
 __device__ __forceinline__ void round_r2(float* buf, int warp, int lane, const Sink& sink)
 {
-    const int p = phys(4 * lane);
-    const int p4 = phys(4 * lane + 4);
+    static_assert(WB % 128 == 0 && PITCH % 4 == 0, "chunked rows");
     for (int pr = warp; pr < R / 2; pr += NWARPS) {
-#pragma unroll 1
+        float* A = buf + (2 * pr) * PITCH + 4 * lane;
+        float* B = A + PITCH;
+#pragma unroll
         for (int xb = 0; xb < WB; xb += 128) {
-            const bool act = xb + 4 * lane < WB;
-            float* A = buf + (2 * pr) * PITCH + phys(xb);
-            float* B = A + PITCH;
             float a[4], b[5];
-            if (act) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k) { a[k] = A[p + k]; b[k] = B[p + k]; }
-                b[4] = B[p4];
-            }
+            ld4(a, A + xb);
+            ld4(b, B + xb);
+            b[4] = B[xb + 4];
             __syncwarp();
-            if (act) {
-                float oa[4], ob[4];
+            float oa[4], ob[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    oa[k] = a[k] + b[k];
-                    ob[k] = a[k] + b[k + 1];
-                }
-                if constexpr (std::is_same<Sink, SmemSink>::value) {
-                    smem_put<PITCH>(A, p, oa);
-                    smem_put<PITCH>(B, p, ob);
-                } else {
-                    sink(2 * pr, xb + 4 * lane, oa);
-                    sink(2 * pr + 1, xb + 4 * lane, ob);
-                }
+            for (int k = 0; k < 4; ++k) {
+                oa[k] = a[k] + b[k];
+                ob[k] = a[k] + b[k + 1];
+            }
+            if constexpr (std::is_same<Sink, SmemSink>::value) {
+                st4(A + xb, oa);
+                st4(B + xb, ob);
+            } else {
+                sink(2 * pr, xb + 4 * lane, oa);
+                sink(2 * pr + 1, xb + 4 * lane, ob);
             }
             __syncwarp();
         }
+    }
+}
+
+// Stages s and s+1 on the quad {a, a+h, a+2h, a+3h} whose first-stage shift is t = tb + T3
+// (tb a multiple of 4).  A..D point at column 4l of the four rows.
+template <int T3, int WB, class Sink>
+__device__ __forceinline__ void quad_r4(float* A, float* B, float* C, float* D, int tb, int a,
+                                        int h, int lane, const Sink& sink)
+{
+    // 16-byte words holding rows B, C, D at columns 4l + t + k, 4l + 2t + k, 4l + 3t + k
+    constexpr int cb = (2 * T3) & ~3, c3 = (2 * T3) & 3;
+    constexpr int db = (3 * T3) & ~3, d3 = (3 * T3) & 3;
+    constexpr bool d_three = d3 + 6 > 7;
+    const float* Bw = B + tb;
+    const float* Cw = C + 2 * tb + cb;
+    const float* Dw = D + 3 * tb + db;
+#pragma unroll
+    for (int xb = 0; xb < WB; xb += 128) {
+        float va[4], wb[8], wc[8], wd[12];
+        ld4(va, A + xb);
+        ld4(wb, Bw + xb);
+        ld4(wb + 4, Bw + xb + 4);
+        ld4(wc, Cw + xb);
+        ld4(wc + 4, Cw + xb + 4);
+        ld4(wd, Dw + xb);
+        ld4(wd + 4, Dw + xb + 4);
+        if constexpr (d_three) ld4(wd + 8, Dw + xb + 8);
+        __syncwarp();
+        // stage s: rows a, a+h from (A, B) with shifts t, t+1; rows a+2h, a+3h from (C, D)
+        // likewise, at the columns stage s+1 will read
+        float x0v[4], x1v[4], y0[5], y1[5];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            x0v[k] = va[k] + wb[T3 + k];
+            x1v[k] = va[k] + wb[T3 + k + 1];
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            y0[k] = wc[c3 + k] + wd[d3 + k];
+            y1[k] = wc[c3 + k + 1] + wd[d3 + k + 2];
+        }
+        // stage s+1: pairs (a, a+2h) with shift 2t and (a+h, a+3h) with shift 2t+1
+        float o0[4], o1[4], o2[4], o3[4];          // rows a, a+h, a+2h, a+3h
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            o0[k] = x0v[k] + y0[k];
+            o2[k] = x0v[k] + y0[k + 1];
+            o1[k] = x1v[k] + y1[k];
+            o3[k] = x1v[k] + y1[k + 1];
+        }
+        if constexpr (std::is_same<Sink, SmemSink>::value) {
+            st4(A + xb, o0);
+            st4(B + xb, o1);
+            st4(C + xb, o2);
+            st4(D + xb, o3);
+        } else {
+            const int x0 = xb + 4 * lane;
+            sink(a, x0, o0);
+            sink(a + h, x0, o1);
+            sink(a + 2 * h, x0, o2);
+            sink(a + 3 * h, x0, o3);
+        }
+        __syncwarp();
     }
 }
 
@@ -180,73 +247,22 @@ __device__ __forceinline__ void round_r2(float* buf, int warp, int lane, const S
 template <int R, int WB, int PITCH, int NWARPS, class Sink>
 __device__ __forceinline__ void round_r4(float* buf, int s, int warp, int lane, const Sink& sink)
 {
+    static_assert(WB % 128 == 0 && PITCH % 4 == 0, "chunked rows");
     const int h = 1 << (s - 1);
     for (int qd = warp; qd < R / 4; qd += NWARPS) {
         const int qlo = qd & (h - 1);
         const int a = ((qd >> (s - 1)) << (s + 1)) | qlo;
         const int t = rev_bits(qlo, s - 1);
-        // phys(xb + y) = phys(xb) + phys(y) for xb a multiple of 32, so each lane's shifted
-        // offsets are computed once per quad and reused for every 128-column chunk.
-        int ob[5], oc[6], od[7];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) ob[k] = phys(4 * lane + t + k);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) oc[k] = phys(4 * lane + 2 * t + k);
-#pragma unroll
-        for (int k = 0; k < 7; ++k) od[k] = phys(4 * lane + 3 * t + k);
-        const int pl = phys(4 * lane);
-#pragma unroll 1
-        for (int xb = 0; xb < WB; xb += 128) {
-            const int x0 = xb + 4 * lane;
-            const bool act = x0 < WB;
-            const int pb = phys(xb);
-            float* A = buf + a * PITCH + pb;
-            float* B = A + h * PITCH;
-            float* C = A + 2 * h * PITCH;
-            float* D = A + 3 * h * PITCH;
-            const int p = pl;
-            float o0[4], o1[4], o2[4], o3[4];          // rows a, a+h, a+2h, a+3h
-            if (act) {
-                float va[4], vb[5], vc[6], vd[7];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) va[k] = A[p + k];
-#pragma unroll
-                for (int k = 0; k < 5; ++k) vb[k] = B[ob[k]];
-#pragma unroll
-                for (int k = 0; k < 6; ++k) vc[k] = C[oc[k]];
-#pragma unroll
-                for (int k = 0; k < 7; ++k) vd[k] = D[od[k]];
-                // stage s: rows a, a+h from (A, B) with shifts t, t+1; rows a+2h, a+3h from
-                // (C, D) likewise, at the columns stage s+1 will read
-                float x0v[4], x1v[4], y0[5], y1[5];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) { x0v[k] = va[k] + vb[k]; x1v[k] = va[k] + vb[k + 1]; }
-#pragma unroll
-                for (int k = 0; k < 5; ++k) { y0[k] = vc[k] + vd[k]; y1[k] = vc[k + 1] + vd[k + 2]; }
-                // stage s+1: pairs (a, a+2h) with shift 2t and (a+h, a+3h) with shift 2t+1
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    o0[k] = x0v[k] + y0[k];
-                    o2[k] = x0v[k] + y0[k + 1];
-                    o1[k] = x1v[k] + y1[k];
-                    o3[k] = x1v[k] + y1[k + 1];
-                }
-            }
-            __syncwarp();
-            if (act) {
-                if constexpr (std::is_same<Sink, SmemSink>::value) {
-                    smem_put<PITCH>(A, p, o0);
-                    smem_put<PITCH>(B, p, o1);
-                    smem_put<PITCH>(C, p, o2);
-                    smem_put<PITCH>(D, p, o3);
-                } else {
-                    sink(a, x0, o0);
-                    sink(a + h, x0, o1);
-                    sink(a + 2 * h, x0, o2);
-                    sink(a + 3 * h, x0, o3);
-                }
-            }
-            __syncwarp();
+        float* A = buf + a * PITCH + 4 * lane;
+        float* B = A + h * PITCH;
+        float* C = A + 2 * h * PITCH;
+        float* D = A + 3 * h * PITCH;
+        const int tb = t & ~3;
+        switch (t & 3) {                                   // the same for the whole warp
+            case 0: quad_r4<0, WB>(A, B, C, D, tb, a, h, lane, sink); break;
+            case 1: quad_r4<1, WB>(A, B, C, D, tb, a, h, lane, sink); break;
+            case 2: quad_r4<2, WB>(A, B, C, D, tb, a, h, lane, sink); break;
+            default: quad_r4<3, WB>(A, B, C, D, tb, a, h, lane, sink); break;
         }
     }
 }
@@ -278,8 +294,10 @@ __device__ __forceinline__ void hough_stages(float* buf, int warp, int lane, con
     }
 }
 
+// Row pitch: the WB columns, the shifted reads' overhang (at most 3 (R/4 - 1) + 11 columns
+// past the last chunk's start word), zero filled; a multiple of 4.
 template <int R, int WB>
-constexpr int hough_pitch() { return phys(WB + 3 * (R / 4) + 8) + 1; }
+constexpr int hough_pitch() { return (WB + 3 * (R / 4) + 8 + 3) & ~3; }
 
 // Pass-2 shared floats: Hough rows, the first quarter's [T2][R+1] result, and for the h
 // quarters the [T2][R] image tile.
@@ -321,6 +339,43 @@ struct Pass1Args {
     int N, K, M, pitch;
 };
 
+// One warp resamples one linogram row over a WB-column tile: lane l computes columns
+// l + 32k at detector positions m0 + k step, angle rows k0 (ra) and k0+1 (ra + pitch) of a
+// filtered sinogram whose rows carry kGuard zero bins on each side.  Each batch of kS
+// samples issues all of its gathers before combining any of them; the arithmetic is
+// linogram_sample's, term for term.  Clamping the bin to [-kGuard, M] keeps bins j and j+1
+// inside the guarded row, and a clamped bin only happens when both true bins lie outside
+// [0, M), where the guards read 0: the result equals zero padding without any select.
+// CLIP zeroes the columns past the trapezoid (column offset 32k > lim).
+template <int WB, bool CLIP>
+__device__ __forceinline__ void resample_row(float* row, const float* ra, int pitch, int M,
+                                             long long m, long long step, float w0, float w1,
+                                             int lim)
+{
+    constexpr int kS = 4;
+#pragma unroll
+    for (int kb = 0; kb < WB / 32; kb += kS) {
+        float l0[kS], l1[kS], l2[kS], l3[kS], fr[kS];
+#pragma unroll
+        for (int k = 0; k < kS; ++k, m += step) {
+            int j;
+            split_fixed(m, j, fr[k]);
+            const float* pp = ra + min(max(j, -kGuard), M);
+            l0[k] = __ldg(pp);
+            l1[k] = __ldg(pp + 1);
+            l2[k] = __ldg(pp + pitch);
+            l3[k] = __ldg(pp + pitch + 1);
+        }
+#pragma unroll
+        for (int k = 0; k < kS; ++k) {
+            const float va = fmaf(fr[k], l1[k] - l0[k], l0[k]);
+            const float vb = fmaf(fr[k], l3[k] - l2[k], l2[k]);
+            const float v = fmaf(w1, vb, w0 * va);
+            row[32 * (kb + k)] = (!CLIP || 32 * (kb + k) <= lim) ? v : 0.0f;
+        }
+    }
+}
+
 // CTA = (column tile, quarter * blocks + block, slice).  Resamples (or loads) the block's
 // 2^LOGR linogram rows over the tile plus halo, runs LOGR stages, writes G.
 template <int LOGR, bool FROM_LIN>
@@ -332,7 +387,7 @@ pass1_kernel(Pass1Args a)
     constexpr int T = WB - R;
     constexpr int PITCH = hough_pitch<R, WB>();
     constexpr int NWARPS = kNT1 / 32;
-    extern __shared__ float buf[];
+    extern __shared__ __align__(16) float buf[];
 
     const int N = a.N, W = 2 * N;
     const int nblocks = N >> LOGR;
@@ -351,14 +406,12 @@ pass1_kernel(Pass1Args a)
             const int i = bi * R + j;
             const int c = c0 + x;
             const bool ok = c <= N - 1 + i;
-            cp_async4(buf + j * PITCH + phys(x), ok ? a.src + (lin_q + i) * W + c : a.src, ok);
+            cp_async4(buf + j * PITCH + x, ok ? a.src + (lin_q + i) * W + c : a.src, ok);
         }
     } else {
-        // One warp per linogram row, lane = column within each 32-column group.  Each batch
-        // of kS samples issues all of its gathers before combining any of them; the
-        // arithmetic is the same as linogram_sample's, term for term.
-        // rows of the filtered sinogram are `pitch` floats apart with kGuard zero bins on
-        // each side; pt points at bin 0 of row 0 of this slice
+        // One warp per linogram row, lane = column within each 32-column group.  Rows of
+        // the filtered sinogram are `pitch` floats apart with kGuard zero bins on each side;
+        // pt points at bin 0 of row 0 of this slice.
         const float* pt = a.src + (size_t)s * a.K * a.pitch + kGuard;
         const int M = a.M;
         const int pitch = a.pitch;
@@ -369,7 +422,7 @@ pass1_kernel(Pass1Args a)
             float* row = buf + j * PITCH + lane;
             if (c0 > limit) {                                  // tile past the trapezoid
 #pragma unroll
-                for (int k = 0; k < WB / 32; ++k) row[33 * k] = 0.0f;
+                for (int k = 0; k < WB / 32; ++k) row[32 * k] = 0.0f;
                 continue;
             }
             const RowGeom gm = a.geom[q * N + i];
@@ -377,32 +430,11 @@ pass1_kernel(Pass1Args a)
             const long long m0 = gm.b_fx + gm.a_fx * (long long)(c0 + lane);
             const long long step = gm.a_fx * 32;
             if (!gm.wrap) {
-                // Angle rows k0 and k0+1 are adjacent.  Clamping the bin to [-kGuard, M]
-                // keeps bins j and j+1 inside the guarded row, and a clamped bin only
-                // happens when both true bins lie outside [0, M), where the guards read 0:
-                // the result equals zero padding without any select.
-                long long m = m0;
-#pragma unroll
-                for (int kb = 0; kb < WB / 32; kb += kS) {
-                    float l0[kS], l1[kS], l2[kS], l3[kS], fr[kS];
-#pragma unroll
-                    for (int k = 0; k < kS; ++k, m += step) {
-                        int j;
-                        split_fixed(m, j, fr[k]);
-                        const float* pp = ra + min(max(j, -kGuard), M);
-                        l0[k] = __ldg(pp);
-                        l1[k] = __ldg(pp + 1);
-                        l2[k] = __ldg(pp + pitch);
-                        l3[k] = __ldg(pp + pitch + 1);
-                    }
-#pragma unroll
-                    for (int k = 0; k < kS; ++k) {
-                        const float va = fmaf(fr[k], l1[k] - l0[k], l0[k]);
-                        const float vb = fmaf(fr[k], l3[k] - l2[k], l2[k]);
-                        const float v = gm.w * fmaf(gm.ft, vb - va, va);
-                        row[33 * (kb + k)] = (c0 + lane + 32 * (kb + k) <= limit) ? v : 0.0f;
-                    }
-                }
+                if (c0 + WB - 1 <= limit)                      // whole tile inside the trapezoid
+                    resample_row<WB, false>(row, ra, pitch, M, m0, step, gm.w0, gm.w1, 0);
+                else
+                    resample_row<WB, true>(row, ra, pitch, M, m0, step, gm.w0, gm.w1,
+                                           limit - c0 - lane);
                 continue;
             }
             const float* rb = pt;                              // wrap: row 0, mirrored
@@ -426,14 +458,14 @@ pass1_kernel(Pass1Args a)
                 for (int k = 0; k < kS; ++k) {
                     const float va = fmaf(fa[k], a1[k] - a0[k], a0[k]);
                     const float vb = fmaf(fb[k], b1[k] - b0[k], b0[k]);
-                    const float v = gm.w * fmaf(gm.ft, vb - va, va);
-                    row[33 * (kb + k)] = (c0 + lane + 32 * (kb + k) <= limit) ? v : 0.0f;
+                    const float v = fmaf(gm.w1, vb, gm.w0 * va);
+                    row[32 * (kb + k)] = (c0 + lane + 32 * (kb + k) <= limit) ? v : 0.0f;
                 }
             }
         }
     }
     for (int j = warp; j < R; j += NWARPS)
-        for (int p = phys(WB) + lane; p < PITCH; p += 32) buf[j * PITCH + p] = 0.0f;
+        for (int p = WB + lane; p < PITCH; p += 32) buf[j * PITCH + p] = 0.0f;
     if (FROM_LIN) cp_async_wait_all();
     __syncthreads();
 
@@ -463,7 +495,7 @@ pass2_kernel(Pass2Args a)
     constexpr int PITCH = hough_pitch<R, WB>();
     constexpr int NWARPS = kNT2 / 32;
     constexpr int TP = R + 1;                  // [T2][R + 1] transposed tile (h quarters)
-    extern __shared__ float buf[];
+    extern __shared__ __align__(16) float buf[];
 
     const int N = a.N, W = 2 * N;
     const int R1 = 1 << a.n1;
@@ -500,10 +532,10 @@ pass2_kernel(Pass2Args a)
             const int x = idx - ih * WB;
             const int col = uo + tau_hi * ih + x;
             const bool ok = col >= 0 && col < N + (tau_hi + 1) * ih;
-            cp_async4(buf + ih * PITCH + phys(x), ok ? gq + ((size_t)ih * R1 + tau_hi) * W + col : gq, ok);
+            cp_async4(buf + ih * PITCH + x, ok ? gq + ((size_t)ih * R1 + tau_hi) * W + col : gq, ok);
         }
         for (int j = warp; j < R; j += NWARPS)
-            for (int p = phys(WB) + lane; p < PITCH; p += 32) buf[j * PITCH + p] = 0.0f;
+            for (int p = WB + lane; p < PITCH; p += 32) buf[j * PITCH + p] = 0.0f;
         cp_async_wait_all();
         __syncthreads();
 
@@ -516,9 +548,9 @@ pass2_kernel(Pass2Args a)
             const int xx = e - j * T2;
             float* f = first + xx * TP + rev_bits(j, LOGR2);
             if (half == 0) {
-                *f = buf[j * PITCH + phys(xx)];
+                *f = buf[j * PITCH + xx];
             } else {
-                const float v = *f + buf[j * PITCH + phys(T2 - 1 - xx)];
+                const float v = *f + buf[j * PITCH + T2 - 1 - xx];
                 if (HORIZ) *f = v;
                 else if (xx < nx) img[(size_t)(tau_hi * R + rev_bits(j, LOGR2)) * N + x0 + xx] = v;
             }

@@ -8,15 +8,15 @@
 //   y(n) = sum_j Re(r_j s_j(n)) + sum_k d_k p(n-k),   s_j(n) = p_j s_j(n-1) + p(n),
 // which stays accurate in float32 where the direct form does not (its poles crowd z = 1).
 //
-// A row is filtered by wpr warps: it is staged once in shared memory (asynchronous
-// coalesced copies) and lane l of warp w owns the chunk of L consecutive samples starting
+// A row is filtered by wpr warps: it is staged once in shared memory (16-byte asynchronous
+// copies at the row's own alignment phase, zero padded past its end) and lane l of warp w owns the chunk of L consecutive samples starting
 // at (32 w + l) L (L odd, at most kIirLmax, so the lanes' strided reads fall in distinct
 // banks).  Each mode is a first-order linear recurrence, so each direction is a blocked
 // scan: every lane runs its chunk from zero state; the end states are combined by a
 // Kogge-Stone scan across the warp (powers p^(L 2^d)) and a Horner sweep across the warps
 // of the row (power p^(32 L), warp totals exchanged in shared memory); every lane then
 // reruns its chunk from its true incoming state.  The anticausal result goes to a second
-// shared row, the causal pass adds to it there, and the sum is written back with coalesced
+// shared row, the causal pass adds to it there, and the sum is written back with 16-byte
 // stores: one HBM read and one write per sample.  Direct taps (absent from the fitted
 // filters) are a compile-time variant.
 #include "fbp_internal.h"
@@ -212,108 +212,172 @@ __device__ __forceinline__ void incoming_state(ModeState<JR, JC>& s, const IirPa
     s = t;
 }
 
-template <int JR, int JC, bool TAPS>
+// Shared-memory floats of one row buffer: every lane's L samples plus one zero past them,
+// rounded up to whole 16-byte groups, plus 3 floats of alignment shift.
+__host__ __device__ inline int row_buffer_floats(int M, int wpr, int L)
+{
+    const int span = max(M, 32 * wpr * L) + 1;
+    return ((span + 3) & ~3) + 4;
+}
+
+// Copy elements [0, M) of a row whose first element has global float index e0 (from a
+// 16-byte-aligned base) between global and shared memory, where the shared row + n is
+// 16-byte aligned exactly when e0 + n is a multiple of 4: scalar head and tail, 16-byte
+// body.  t is the row's thread index, nthr the row's thread count.  Loads are asynchronous
+// copies (all in flight at once; the caller waits with cp.async.wait_all).
+__device__ __forceinline__ void cp_async16(float* dst, const float* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void load_row(float* dst, const float* src, long long e0, int M,
+                                         int t, int nthr)
+{
+    const int h = min((int)((4 - (e0 & 3)) & 3), M);
+    const int groups = (M - h) >> 2;
+    for (int g = t; g < groups; g += nthr) cp_async16(dst + h + 4 * g, src + h + 4 * g);
+    const int tail0 = h + 4 * groups;
+    if (t < h) cp_async4(dst + t, src + t);
+    if (t < M - tail0) cp_async4(dst + tail0 + t, src + tail0 + t);
+}
+
+__device__ __forceinline__ void store_row(float* dst, const float* src, long long e0, int M,
+                                          int t, int nthr)
+{
+    const int h = min((int)((4 - (e0 & 3)) & 3), M);
+    const int groups = (M - h) >> 2;
+    const float4* s4 = reinterpret_cast<const float4*>(src + h);
+    float4* d4 = reinterpret_cast<float4*>(dst + h);
+    for (int g = t; g < groups; g += nthr) d4[g] = s4[g];
+    const int tail0 = h + 4 * groups;
+    if (t < h) dst[t] = src[t];
+    if (t < M - tail0) dst[tail0 + t] = src[tail0 + t];
+}
+
+// LT > 0: every lane filters exactly LT samples (the plan's L), loops fully unrolled; LT = 0:
+// runtime L.  Lanes past the end of the row filter the zero padding of the shared row.
+// in may equal out (each CTA reads its rows completely before it writes them).
+template <int JR, int JC, bool TAPS, int LT>
 __global__ void __launch_bounds__(kIirThreads)
-iir_ramp_kernel(const float* in, float* out, int rows, int M, int out_pitch, int rows_per_cta,
-                IirParams prm)
+iir_ramp_kernel(const float* in, float* out, int rows, int M,
+                int out_pitch, int rows_per_cta, IirParams prm)
 {
     constexpr int SF = state_floats<JR, JC>();
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) float smem[];
     const int wpr = prm.wpr;
+    const int L = LT > 0 ? LT : prm.L;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int rloc = warp / wpr;
     const int w = warp - rloc * wpr;
+    const int t = w * 32 + lane;                 // thread index within the row
+    const int nthr = 32 * wpr;
     const long long row = (long long)blockIdx.x * rows_per_cta + rloc;
-    const bool live = rloc < rows_per_cta && row < rows;
-    // per row: input samples sp[M], result sz[M]; then the warp totals of both directions
-    float* sp = smem + (size_t)rloc * 2 * M;
-    float* sz = sp + M;
-    float* tot = smem + (size_t)rows_per_cta * 2 * M + (size_t)rloc * 2 * wpr * SF;
+    const bool live = row < rows;
+    const int rb = row_buffer_floats(M, wpr, L);
+    // per row: staged input sp, result sz (each shifted to the global 16-byte phase of its
+    // row), then the warp totals of both directions
+    const long long e_in = row * (long long)M;
+    const int lead = (out_pitch - M) / 2;
+    const long long e_out = row * (long long)out_pitch + lead;
+    float* sp = smem + (size_t)rloc * 2 * rb + (e_in & 3);
+    float* sz = smem + (size_t)rloc * 2 * rb + rb + (e_out & 3);
+    float* tot = smem + (size_t)rows_per_cta * 2 * rb + (size_t)rloc * 2 * wpr * SF;
+    const int span = nthr * L;
 
     if (live) {
-        const float* src = in + row * (long long)M;
-        for (int n = w * 32 + lane; n < M; n += 32 * wpr) {
-            const unsigned d = (unsigned)__cvta_generic_to_shared(sp + n);
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src + n) : "memory");
-        }
+        load_row(sp, in + e_in, e_in, M, t, nthr);
+        for (int n = M + t; n <= span; n += nthr) sp[n] = 0.0f;
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
 
-    const int L = prm.L;
-    const int n0 = live ? min((w * 32 + lane) * L, M) : M;
-    const int n1 = min(n0 + L, M);
+    const int n0 = live ? t * L : 0;      // a dead row runs no sample loop, only the scans
     // Mode input: x(n) - x(n-1) causally and x(n) - x(n+1) anticausally when the plan
     // factored (1 - z^-1) out of the numerator, else x(n); x = 0 outside [0, M).
     const float dmask = prm.diff ? 1.0f : 0.0f;
     auto xs = [&](int m) { return (m >= 0 && m < M) ? sp[m] : 0.0f; };
-    const float right = xs(n1);
-    const float left = xs(n0 - 1);
+    const float* x = sp + n0;
+    float* z = sz + n0;
+    const float right = live ? x[L] : 0.0f;
+    const float left = (live && n0 > 0) ? x[-1] : 0.0f;
     ModeState<JR, JC> s;
 
     // anticausal: local pass from zero state (right to left), scan, final pass into sz
     zero_state(s);
     float nb = right;
-#pragma unroll 4
-    for (int n = n1 - 1; n >= n0; --n) {
-        const float xv = sp[n];
-        step(s, prm, fmaf(-dmask, nb, xv));
-        nb = xv;
+    if (live) {
+#pragma unroll (LT > 0 ? LT : 4)
+        for (int i = L - 1; i >= 0; --i) {
+            const float xv = x[i];
+            step(s, prm, fmaf(-dmask, nb, xv));
+            nb = xv;
+        }
     }
     incoming_state<JR, JC, false>(s, prm, tot + wpr * SF, w, lane);
-    nb = right;
-#pragma unroll 4
-    for (int n = n1 - 1; n >= n0; --n) {
-        const float xv = sp[n];
-        step(s, prm, fmaf(-dmask, nb, xv));
-        nb = xv;
-        float z = output(s, prm);
-        if constexpr (TAPS) {
-            for (int t = 0; t < prm.nd; ++t)
-                z = fmaf(prm.d[t], fmaf(-dmask, xs(n + t + 1), xs(n + t)), z);
+    if (live) {
+        nb = right;
+#pragma unroll (LT > 0 ? LT : 4)
+        for (int i = L - 1; i >= 0; --i) {
+            const float xv = x[i];
+            step(s, prm, fmaf(-dmask, nb, xv));
+            nb = xv;
+            float o = output(s, prm);
+            if constexpr (TAPS) {
+                const int n = n0 + i;
+                for (int k = 0; k < prm.nd; ++k)
+                    o = fmaf(prm.d[k], fmaf(-dmask, xs(n + k + 1), xs(n + k)), o);
+            }
+            z[i] = o;
         }
-        sz[n] = z;
     }
 
     // causal: local pass, scan, final pass adding y to the anticausal z
     zero_state(s);
     float pb = left;
-#pragma unroll 4
-    for (int n = n0; n < n1; ++n) {
-        const float xv = sp[n];
-        step(s, prm, fmaf(-dmask, pb, xv));
-        pb = xv;
+    if (live) {
+#pragma unroll (LT > 0 ? LT : 4)
+        for (int i = 0; i < L; ++i) {
+            const float xv = x[i];
+            step(s, prm, fmaf(-dmask, pb, xv));
+            pb = xv;
+        }
     }
     incoming_state<JR, JC, true>(s, prm, tot, w, lane);
-    pb = left;
-#pragma unroll 4
-    for (int n = n0; n < n1; ++n) {
-        const float xv = sp[n];
-        step(s, prm, fmaf(-dmask, pb, xv));
-        pb = xv;
-        float y = output(s, prm);
-        if constexpr (TAPS) {
-            for (int t = 0; t < prm.nd; ++t)
-                y = fmaf(prm.d[t], fmaf(-dmask, xs(n - t - 1), xs(n - t)), y);
+    if (live) {
+        pb = left;
+#pragma unroll (LT > 0 ? LT : 4)
+        for (int i = 0; i < L; ++i) {
+            const float xv = x[i];
+            step(s, prm, fmaf(-dmask, pb, xv));
+            pb = xv;
+            float o = output(s, prm);
+            if constexpr (TAPS) {
+                const int n = n0 + i;
+                for (int k = 0; k < prm.nd; ++k)
+                    o = fmaf(prm.d[k], fmaf(-dmask, xs(n - k - 1), xs(n - k)), o);
+            }
+            z[i] = o + z[i];
         }
-        sz[n] = y + sz[n];
     }
     __syncthreads();
 
     if (live) {
-        const int lead = (out_pitch - M) / 2;
-        float* dst = out + row * (long long)out_pitch;
-        if (w == 0) {
-            if (lane < lead) dst[lane] = 0.0f;
-            if (lane < out_pitch - M - lead) dst[lead + M + lane] = 0.0f;
-        }
-        dst += lead;
-        for (int n = w * 32 + lane; n < M; n += 32 * wpr) dst[n] = sz[n];
+        float* dst = out + e_out;
+        if (t < lead) dst[t - lead] = 0.0f;
+        if (t < out_pitch - M - lead) dst[M + t] = 0.0f;
+        store_row(dst, sz, e_out, M, t, nthr);
     }
 }
 
-template <int JR, int JC, bool TAPS>
+template <int JR, int JC, bool TAPS, int LT>
 cudaError_t launch_iir_t(const fbp_plan_s* p, const float* in, float* out, int rows,
                          int out_pitch, cudaStream_t st)
 {
@@ -321,21 +385,25 @@ cudaError_t launch_iir_t(const fbp_plan_s* p, const float* in, float* out, int r
     const int wpr = p->iir.wpr;
     const int rows_per_cta = wpr <= kIirThreads / 32 ? kIirThreads / 32 / wpr : 1;
     const int threads = 32 * wpr * rows_per_cta;
-    const size_t smem = ((size_t)rows_per_cta * 2 * p->M + (size_t)rows_per_cta * 2 * wpr * SF) * sizeof(float);
+    const size_t rb = (size_t)row_buffer_floats(p->M, wpr, p->iir.L);
+    const size_t smem = ((size_t)rows_per_cta * 2 * rb + (size_t)rows_per_cta * 2 * wpr * SF) * sizeof(float);
     if (smem > (size_t)kMaxSmem || threads > 1024) return cudaErrorInvalidValue;
     const int grid = (rows + rows_per_cta - 1) / rows_per_cta;
-    iir_ramp_kernel<JR, JC, TAPS><<<grid, threads, smem, st>>>(in, out, rows, p->M, out_pitch,
-                                                               rows_per_cta, p->iir);
+    iir_ramp_kernel<JR, JC, TAPS, LT><<<grid, threads, smem, st>>>(in, out, rows, p->M, out_pitch,
+                                                                   rows_per_cta, p->iir);
     return cudaGetLastError();
 }
 
 template <int JR, int JC>
 cudaError_t set_attr()
 {
-    cudaError_t e = cudaFuncSetAttribute(iir_ramp_kernel<JR, JC, false>,
+    cudaError_t e = cudaFuncSetAttribute(iir_ramp_kernel<JR, JC, false, 0>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(iir_ramp_kernel<JR, JC, true>,
+        e = cudaFuncSetAttribute(iir_ramp_kernel<JR, JC, true, 0>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(iir_ramp_kernel<JR, JC, false, kIirLmax>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     return e;
 }
@@ -366,8 +434,9 @@ cudaError_t launch_iir(const fbp_plan_s* p, const float* in, float* out, int row
     const int jr = p->iir.jr, jc = p->iir.jc;
 #define FBP_X(R, C)                                                                   \
     if (jr == R && jc == C)                                                           \
-        return p->iir.nd > 0 ? launch_iir_t<R, C, true>(p, in, out, rows, out_pitch, st)  \
-                             : launch_iir_t<R, C, false>(p, in, out, rows, out_pitch, st);
+        return p->iir.nd > 0 ? launch_iir_t<R, C, true, 0>(p, in, out, rows, out_pitch, st)        \
+             : p->iir.L == kIirLmax ? launch_iir_t<R, C, false, kIirLmax>(p, in, out, rows, out_pitch, st) \
+                                    : launch_iir_t<R, C, false, 0>(p, in, out, rows, out_pitch, st);
     FBP_IIR_MODES(FBP_X)
 #undef FBP_X
     return cudaErrorInvalidValue;

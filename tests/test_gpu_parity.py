@@ -72,7 +72,7 @@ def test_iir_filter_matches_oracle(fbp, torch, coeff_table, N, order, noise):
     assert np.abs(got - want).max() <= TOL_IIR * np.abs(want).max()
 
 
-@pytest.mark.parametrize("M", [2, 3, 31, 32, 33, 95, 1000, 5793])
+@pytest.mark.parametrize("M", [2, 3, 31, 32, 33, 95, 725, 1000, 2897, 5793])
 def test_iir_filter_ragged_rows(fbp, torch, coeff_table, M):
     rng = np.random.default_rng(M)
     s = rng.normal(size=(2, 5, M)).astype(np.float32)
@@ -85,6 +85,13 @@ def test_iir_filter_ragged_rows(fbp, torch, coeff_table, M):
 def test_iir_filter_pure_fir_and_complex_poles(fbp, torch):
     rng = np.random.default_rng(3)
     s = rng.normal(size=(1, 7, 300)).astype(np.float32)
+    # 2897 samples per row: lanes of 23 samples (the unrolled kernel variant)
+    s2 = rng.normal(size=(1, 5, 2897)).astype(np.float32)
+    for co in ([0.1, 0.2, -0.3], list(np.real(np.poly([0.6 + 0.5j, 0.6 - 0.5j, 0.3]))[1:])), \
+              ([0.2, -0.1, 0.05], list(np.real(np.poly([0.9 + 0.2j, 0.9 - 0.2j, -0.4, 0.5]))[1:])):
+        got = gpu_filter(fbp, torch, s2, 2048, co)
+        want = oracle.iir_filter(s2.astype(np.float64), *co)
+        assert np.abs(got - want).max() <= TOL_IIR * np.abs(want).max()
     for co in (([0.25, -0.5, 0.25], []),                                   # no feedback
                ([0.1, 0.2, -0.3], list(np.real(np.poly([0.6 + 0.5j, 0.6 - 0.5j, 0.3]))[1:])),
                ([0.3, -0.1, 0.05, 0.02, -0.01], [-0.5, 0.06])):           # direct taps
