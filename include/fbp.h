@@ -77,7 +77,8 @@ fbp_status fbp_default_coeffs(int N, int order, fbp_iir_coeffs* out);
 
 /* Create a plan for slices of an N x N image from K angles x M bins, `batch` slices per
  * call.  coeffs == NULL selects fbp_default_coeffs(N, 0).  fuse_k is the number of Hough
- * stages done by the first back-projection pass (1..6; 0 chooses).  The plan builds its
+ * stages done by the first back-projection pass (1..6, at least 2 when it leaves stages to a
+ * second pass, which takes at most 6; 0 chooses).  The plan builds its
  * per-row geometry tables (Eq. 14-15) on the host in float64 and uploads them; it
  * allocates no workspace yet.  The current CUDA device at creation is the plan's device.
  * Errors: FBP_ERR_INVALID_ARG, FBP_ERR_UNSUPPORTED, FBP_ERR_OOM, FBP_ERR_CUDA. */

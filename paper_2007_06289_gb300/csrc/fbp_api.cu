@@ -463,7 +463,9 @@ fbp_status fbp_plan(fbp_plan_t* out, int N, int K, int M, int batch,
         n1 = fuse_k < n ? fuse_k : n;
     }
     n2 = n - n1;
-    if (n2 > 6) return FBP_ERR_UNSUPPORTED;
+    // a second pass needs first-pass blocks of at least 4 rows (its rows then fit the
+    // 2N-float G rows with their 16-byte alignment shift)
+    if (n2 > 6 || (n2 > 0 && n1 < 2)) return FBP_ERR_UNSUPPORTED;
 
     fbp_plan_s* p = new (std::nothrow) fbp_plan_s();
     if (!p) return FBP_ERR_OOM;

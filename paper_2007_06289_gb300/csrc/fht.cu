@@ -20,7 +20,8 @@
 // Splitting n = n1 + n2, i = i_hi 2^n1 + i_lo, tau = tau_hi 2^n2 + tau_lo, the pattern
 // separates as d_tau(i) = d_{tau_hi}(i_lo) + tau_hi i_hi + d_{tau_lo}(i_hi), so the
 // transform runs in two passes, each a small transform in shared memory:
-//   pass 1: every block of 2^n1 consecutive rows -> G[i_hi][tau_hi][v]
+//   pass 1: every block of 2^n1 consecutive rows -> G[i_hi][tau_hi][v] (each row stored
+//           shifted by 0..3 columns so that pass 2 starts its reads on 16-byte words)
 //   pass 2: for each tau_hi, the 2^n2 rows G[.][tau_hi] sheared by tau_hi * i_hi columns
 // (the shear is just a per-row load offset).  Every partial sum is the same float32 sum
 // as in the stage recursion, so the result is reproducible bit for bit.
@@ -38,6 +39,8 @@ namespace {
 constexpr int kWB1 = 256;      // pass-1 tile width including the halo of 2^n1 columns
 constexpr int kNT1 = 512;      // pass-1 threads
 constexpr int kNT2 = 256;      // pass-2 threads
+constexpr int kWB2 = 256;      // pass-2 row width: tile plus halo
+constexpr unsigned kFull = 0xffffffffu;
 
 __device__ __forceinline__ int rev_bits(int v, int bits)
 {
@@ -131,9 +134,10 @@ resample_kernel(const float* __restrict__ filt, float* __restrict__ lin,
 // picks the values in registers; the pick depends only on t mod 4, which is the same for the
 // whole warp, so each of the four cases is compiled separately.
 //
-// A round hands each thread's results -- four consecutive columns x0..x0+3 of one row --
-// to a sink.  SmemSink writes them back in place (every round but a pass's last); a pass
-// may give its last round a sink that stores straight to global memory.
+// A round hands each thread's results -- four consecutive columns x0..x0+3 of one row,
+// the row being the slot-th of the warp's pair or quad -- to a sink.  SmemSink writes them
+// back in place (every round but a pass's last); a pass may give its last round a sink that
+// stores straight to global memory.  Every lane of the warp calls the sink together.
 struct SmemSink {};
 
 __device__ __forceinline__ void ld4(float* v, const float* p)
@@ -172,8 +176,8 @@ __device__ __forceinline__ void round_r2(float* buf, int warp, int lane, const S
                 st4(A + xb, oa);
                 st4(B + xb, ob);
             } else {
-                sink(2 * pr, xb + 4 * lane, oa);
-                sink(2 * pr + 1, xb + 4 * lane, ob);
+                sink(0, 2 * pr, xb + 4 * lane, oa);
+                sink(1, 2 * pr + 1, xb + 4 * lane, ob);
             }
             __syncwarp();
         }
@@ -234,10 +238,10 @@ __device__ __forceinline__ void quad_r4(float* A, float* B, float* C, float* D, 
             st4(D + xb, o3);
         } else {
             const int x0 = xb + 4 * lane;
-            sink(a, x0, o0);
-            sink(a + h, x0, o1);
-            sink(a + 2 * h, x0, o2);
-            sink(a + 3 * h, x0, o3);
+            sink(0, a, x0, o0);
+            sink(1, a + h, x0, o1);
+            sink(2, a + 2 * h, x0, o2);
+            sink(3, a + 3 * h, x0, o3);
         }
         __syncwarp();
     }
@@ -299,34 +303,68 @@ __device__ __forceinline__ void hough_stages(float* buf, int warp, int lane, con
 template <int R, int WB>
 constexpr int hough_pitch() { return (WB + 3 * (R / 4) + 8 + 3) & ~3; }
 
-// Pass-2 shared floats: Hough rows, the first quarter's [T2][R+1] result, and for the h
-// quarters the [T2][R] image tile.
-template <int LOGR2, int T2, bool HORIZ>
+// Pass-2 shared floats: the Hough rows of both quarters, the second quarter's rows reused
+// for the h quarters' [T2][R+1] transposed result tile.
+template <int LOGR2, int T2>
 constexpr int pass2_floats()
 {
     constexpr int R = 1 << LOGR2;
-    return R * hough_pitch<R, T2 + R>() + T2 * (R + 1) + (HORIZ ? T2 * R : 0);
+    constexpr int rows = R * hough_pitch<R, kWB2>();
+    return rows + (rows > T2 * (R + 1) ? rows : T2 * (R + 1));
 }
 
+// Tile width of a pass (columns it outputs): the 256-column row minus a halo of at least the
+// block's slope count, a multiple of 4 so that tiles start on 16-byte words.
+template <int R>
+constexpr int tile_width() { return 256 - (R > 4 ? R : 4); }
+
 // ------------------------------------------------------------------------ pass 1
-// Last-round sink of pass 1: slot row j holds slope tau = rev(j); its columns c0 + x0..+3
-// go straight to G row tau of the block, within the region the second pass reads.
-struct GSink {
-    float* rows;        // G row 0 of this (slice, quarter, block)
-    int W, T, c0, N, bi, logr;
-    __device__ __forceinline__ void operator()(int j, int x0, const float (&o)[4]) const
+// G row layout.  Pass-1 row (block bi, slope tau) holds logical column v at storage index
+// v + sh with sh = (-tau bi) mod 4.  The second pass reads that row from v = u0 + tau bi on
+// (u0 a multiple of 4), which is then storage u0 + tau bi + sh, a multiple of 4: it copies
+// whole 16-byte words.  Only storage [sh, need + sh) is written, need = N + (tau+1) bi.
+__device__ __forceinline__ int g_shift(int tau, int bi) { return (-tau * bi) & 3; }
+
+// Last-round sink of pass 1: slot row j holds slope tau = rev(j); its outputs x < T (the
+// rest is halo) within the needed region go to G row tau of the block at storage offset
+// x + sh from the tile start, sh = g_shift(tau, bi).  The 16-byte word at storage offset x0
+// holds x0 - sh .. x0 - sh + 3: the lane's own first 4 - sh values and the last sh of the
+// lane before it (for lane 0: lane 31's of the previous 128-column chunk, kept in `carry`),
+// moved by warp shuffles.  Partial words at the ends of the region go element by element.
+struct GShiftSink {
+    float* rows;            // storage offset 0 of G row 0 of this (slice, quarter, block) tile
+    int W, T, c0, N, bi, logr, lane;
+    mutable float carry[4][3];
+    __device__ __forceinline__ void operator()(int slot, int j, int x0, const float (&o)[4]) const
     {
-        if (x0 >= T) return;                           // halo columns: not outputs
+        const int src_lane = (lane + 31) & 31;
+        const float r1 = __shfl_sync(kFull, o[1], src_lane);
+        const float r2 = __shfl_sync(kFull, o[2], src_lane);
+        const float r3 = __shfl_sync(kFull, o[3], src_lane);
+        const float p1 = lane == 0 ? carry[slot][0] : r1;
+        const float p2 = lane == 0 ? carry[slot][1] : r2;
+        const float p3 = lane == 0 ? carry[slot][2] : r3;
+        carry[slot][0] = r1;
+        carry[slot][1] = r2;
+        carry[slot][2] = r3;
         const int tau = rev_bits(j, logr);
-        const int c = c0 + x0;
-        const int need = N + (tau + 1) * bi;
-        float* dst = rows + (size_t)tau * W + c;
-        if ((c & 3) == 0 && c + 4 <= need) {
-            *reinterpret_cast<float4*>(dst) = make_float4(o[0], o[1], o[2], o[3]);
+        const int sh = g_shift(tau, bi);
+        const int send = min(T, N + (tau + 1) * bi - c0) + sh;   // storage offsets [sh, send)
+        if (x0 >= send) return;
+        float v[4];
+        switch (sh) {                                  // the same for the whole warp
+            case 0: v[0] = o[0]; v[1] = o[1]; v[2] = o[2]; v[3] = o[3]; break;
+            case 1: v[0] = p3; v[1] = o[0]; v[2] = o[1]; v[3] = o[2]; break;
+            case 2: v[0] = p2; v[1] = p3; v[2] = o[0]; v[3] = o[1]; break;
+            default: v[0] = p1; v[1] = p2; v[2] = p3; v[3] = o[0]; break;
+        }
+        float* dst = rows + (size_t)tau * W + x0;
+        if (x0 >= sh && x0 + 4 <= send) {
+            st4(dst, v);
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if (c + k < need) dst[k] = o[k];
+                if (x0 + k >= sh && x0 + k < send) dst[k] = v[k];
         }
     }
 };
@@ -379,12 +417,12 @@ __device__ __forceinline__ void resample_row(float* row, const float* ra, int pi
 // CTA = (column tile, quarter * blocks + block, slice).  Resamples (or loads) the block's
 // 2^LOGR linogram rows over the tile plus halo, runs LOGR stages, writes G.
 template <int LOGR, bool FROM_LIN>
-__global__ void __launch_bounds__(kNT1)
+__global__ void __launch_bounds__(kNT1, 2)
 pass1_kernel(Pass1Args a)
 {
     constexpr int R = 1 << LOGR;
     constexpr int WB = kWB1;
-    constexpr int T = WB - R;
+    constexpr int T = tile_width<R>();
     constexpr int PITCH = hough_pitch<R, WB>();
     constexpr int NWARPS = kNT1 / 32;
     extern __shared__ __align__(16) float buf[];
@@ -469,7 +507,7 @@ pass1_kernel(Pass1Args a)
     if (FROM_LIN) cp_async_wait_all();
     __syncthreads();
 
-    const GSink out{a.g + (lin_q + (size_t)bi * R) * W, W, T, c0, N, bi, LOGR};
+    const GShiftSink out{a.g + (lin_q + (size_t)bi * R) * W + c0, W, T, c0, N, bi, LOGR, lane, {}};
     hough_stages<LOGR, WB, PITCH, NWARPS>(buf, warp, lane, out);
 }
 
@@ -480,22 +518,46 @@ struct Pass2Args {
     int N, n1;
 };
 
+// 16-byte asynchronous copy; src_bytes = 0 writes zeros (src is then not read).
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, int src_bytes)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <int N_PENDING>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N_PENDING) : "memory");
+}
+
 // CTA = (tile of T2 intercepts u, slope group tau_hi, slice).  Runs the second pass for the
 // '-' quarter on u in [x0, x0+T2) and for the '+' quarter on the mirrored range, adds them
 // (F_- + F_+), and either stores the sum into the image (v quarters: [y = tau][x = u]) or
 // adds it to the image through a shared-memory transpose (h quarters: [y = u][x = tau]).
 // Launched for the v quarters first and the h quarters second, so each pixel ends as
-// (F_v- + F_v+) + (F_h- + F_h+).
+// (F_v- + F_v+) + (F_h- + F_h+).  Both quarters' rows are requested up front (one copy
+// group each), so the second quarter's copies run behind the first quarter's stages.
 template <int LOGR2, int T2, bool HORIZ>
-__global__ void __launch_bounds__(kNT2)
+__global__ void __launch_bounds__(kNT2, 3)
 pass2_kernel(Pass2Args a)
 {
     constexpr int R = 1 << LOGR2;
-    constexpr int WB = T2 + R;                 // two 128-column chunks
+    constexpr int WB = kWB2;                   // two 128-column chunks: tile plus halo
+    static_assert(T2 + R <= WB && T2 % 4 == 0, "pass-2 tile");
     constexpr int PITCH = hough_pitch<R, WB>();
     constexpr int NWARPS = kNT2 / 32;
     constexpr int TP = R + 1;                  // [T2][R + 1] transposed tile (h quarters)
     extern __shared__ __align__(16) float buf[];
+    float* const hb0 = buf;                    // '-' quarter rows
+    float* const hb1 = buf + R * PITCH;        // '+' quarter rows, later the transposed tile
 
     const int N = a.N, W = 2 * N;
     const int R1 = 1 << a.n1;
@@ -506,19 +568,6 @@ pass2_kernel(Pass2Args a)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* img = a.img + (size_t)s * N * N;
 
-    // Shared layout: Hough rows | first-quarter result | (h only) the stored v tile.
-    float* first = buf + R * PITCH;                        // T2 * (R + 1) floats
-    float* vtile = first + T2 * TP;
-    // h quarters add to the image tile [y = x0 .. x0+nx) x [x = tau_hi R .. +R) that the v
-    // launch stored: fetch it now, behind the Hough work.
-    if (HORIZ) {
-        for (int e = threadIdx.x; e < nx * R; e += kNT2) {
-            const int xx = e / R;
-            const int tl = e - xx * R;
-            cp_async4(vtile + e, img + (size_t)(x0 + xx) * N + tau_hi * R + tl, true);
-        }
-    }
-
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
         const int q = (HORIZ ? 2 : 0) + half;
@@ -527,42 +576,95 @@ pass2_kernel(Pass2Args a)
         // only feed intercepts outside the image)
         const int uo = half == 0 ? x0 : N - x0 - T2;
         const float* gq = a.g + ((size_t)s * 4 + q) * N * W;
-        for (int idx = threadIdx.x; idx < R * WB; idx += kNT2) {
-            const int ih = idx / WB;
-            const int x = idx - ih * WB;
-            const int col = uo + tau_hi * ih + x;
-            const bool ok = col >= 0 && col < N + (tau_hi + 1) * ih;
-            cp_async4(buf + ih * PITCH + x, ok ? gq + ((size_t)ih * R1 + tau_hi) * W + col : gq, ok);
+        float* hb = half == 0 ? hb0 : hb1;
+        for (int ih = warp; ih < R; ih += NWARPS) {
+            // row (ih, tau_hi) from logical column uo + tau_hi ih on: storage sb + x, with the
+            // stored columns [sh, need + sh)
+            const int sh = g_shift(tau_hi, ih);
+            const int lo = sh;
+            const int hi = N + (tau_hi + 1) * ih + sh;
+            const int sb = uo + tau_hi * ih + sh;
+            const float* grow = gq + ((size_t)ih * R1 + tau_hi) * W;
+            float* drow = hb + ih * PITCH;
+#pragma unroll
+            for (int m = lane; m < WB / 4; m += 32) {
+                const int st = sb + 4 * m;
+                if (st >= lo && st + 4 <= hi) {
+                    cp_async16(drow + 4 * m, grow + st, 16);
+                } else if (st + 4 <= lo || st >= hi) {
+                    cp_async16(drow + 4 * m, grow, 0);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const bool ok = st + k >= lo && st + k < hi;
+                        cp_async4(drow + 4 * m + k, ok ? grow + st + k : grow, ok);
+                    }
+                }
+            }
+            for (int p = WB + lane; p < PITCH; p += 32) drow[p] = 0.0f;
         }
-        for (int j = warp; j < R; j += NWARPS)
-            for (int p = WB + lane; p < PITCH; p += 32) buf[j * PITCH + p] = 0.0f;
-        cp_async_wait_all();
-        __syncthreads();
+        cp_async_commit();
+    }
+    cp_async_wait_group<1>();
+    __syncthreads();
+    hough_stages<LOGR2, WB, PITCH, NWARPS>(hb0, warp, lane, SmemSink{});
+    cp_async_wait_group<0>();
+    __syncthreads();
+    hough_stages<LOGR2, WB, PITCH, NWARPS>(hb1, warp, lane, SmemSink{});
 
-        hough_stages<LOGR2, WB, PITCH, NWARPS>(buf, warp, lane, SmemSink{});
-
-        // first quarter: park F_- at [xx][tau_lo]; second quarter: F_- + F_+, stored to the
-        // image rows (v) or accumulated in place for the transposed write (h)
-        for (int e = threadIdx.x; e < R * T2; e += kNT2) {
-            const int j = e / T2;
-            const int xx = e - j * T2;
-            float* f = first + xx * TP + rev_bits(j, LOGR2);
-            if (half == 0) {
-                *f = buf[j * PITCH + xx];
-            } else {
-                const float v = *f + buf[j * PITCH + T2 - 1 - xx];
-                if (HORIZ) *f = v;
-                else if (xx < nx) img[(size_t)(tau_hi * R + rev_bits(j, LOGR2)) * N + x0 + xx] = v;
+    // F_- + F_+ for slot row j (slope tau_lo = rev(j)) at intercept x0 + xx: columns xx of
+    // hb0 and T2-1-xx of hb1, taken as 16-byte words (the second one reversed).
+    if constexpr (!HORIZ) {
+        for (int j = warp; j < R; j += NWARPS) {
+            float* out = img + (size_t)(tau_hi * R + rev_bits(j, LOGR2)) * N + x0;
+            const float* r0 = hb0 + j * PITCH;
+            const float* r1 = hb1 + j * PITCH;
+            for (int xx = 4 * lane; xx < nx; xx += 128) {
+                float va[4], vb[4], o[4];
+                ld4(va, r0 + xx);
+                ld4(vb, r1 + T2 - 4 - xx);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) o[k] = va[k] + vb[3 - k];
+                st4(out + xx, o);
+            }
+        }
+    } else {
+        // h quarters: the sums in place into hb0, then transposed into [xx][tau_lo] (in
+        // hb1's space), then added to image rows x0 + xx, columns tau_hi R .. + R.
+        for (int j = warp; j < R; j += NWARPS) {
+            float* r0 = hb0 + j * PITCH;
+            const float* r1 = hb1 + j * PITCH;
+            for (int xx = 4 * lane; xx < T2; xx += 128) {
+                float va[4], vb[4], o[4];
+                ld4(va, r0 + xx);
+                ld4(vb, r1 + T2 - 4 - xx);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) o[k] = va[k] + vb[3 - k];
+                st4(r0 + xx, o);
             }
         }
         __syncthreads();
-    }
-
-    if (HORIZ) {
-        for (int e = threadIdx.x; e < nx * R; e += kNT2) {
-            const int xx = e / R;
-            const int tl = e - xx * R;
-            img[(size_t)(x0 + xx) * N + tau_hi * R + tl] = vtile[e] + first[xx * TP + tl];
+        float* tt = hb1;
+        for (int tl = warp; tl < R; tl += NWARPS) {
+            const float* r0 = hb0 + rev_bits(tl, LOGR2) * PITCH;
+            for (int xx = lane; xx < nx; xx += 32) tt[xx * TP + tl] = r0[xx];
+        }
+        __syncthreads();
+        // read-modify-write of the image rows, a batch of kB rows per warp at a time so that
+        // the batch's loads are in flight together
+        constexpr int kB = 7;
+        for (int xb = warp; xb < nx; xb += NWARPS * kB) {
+            for (int tl = lane; tl < R; tl += 32) {
+                float* out = img + (size_t)(x0 + xb) * N + tau_hi * R + tl;
+                const float* src = tt + xb * TP + tl;
+                float v[kB];
+#pragma unroll
+                for (int u = 0; u < kB; ++u)
+                    if (xb + NWARPS * u < nx) v[u] = out[(size_t)NWARPS * u * N];
+#pragma unroll
+                for (int u = 0; u < kB; ++u)
+                    if (xb + NWARPS * u < nx) out[(size_t)NWARPS * u * N] = v[u] + src[NWARPS * u * TP];
+            }
         }
     }
 }
@@ -588,15 +690,15 @@ combine_kernel(const float* __restrict__ g, float* __restrict__ img, int N)
 template <int LOGR>
 constexpr size_t pass1_smem() { return (size_t)(1 << LOGR) * hough_pitch<(1 << LOGR), kWB1>() * sizeof(float); }
 
-template <int LOGR2, int T2, bool HORIZ>
-constexpr size_t pass2_smem() { return (size_t)pass2_floats<LOGR2, T2, HORIZ>() * sizeof(float); }
+template <int LOGR2, int T2>
+constexpr size_t pass2_smem() { return (size_t)pass2_floats<LOGR2, T2>() * sizeof(float); }
 
 template <int LOGR, bool FROM_LIN>
 cudaError_t launch_pass1_t(const fbp_plan_s* p, const float* src, float* g, int count,
                            cudaStream_t st)
 {
     constexpr int R = 1 << LOGR;
-    constexpr int T = kWB1 - R;
+    constexpr int T = tile_width<R>();
     const int nblocks = p->N >> LOGR;
     const int max_cols = p->N + R * (nblocks - 1);
     dim3 grid((max_cols + T - 1) / T, 4 * nblocks, count);
@@ -611,7 +713,7 @@ cudaError_t launch_pass2_t(const fbp_plan_s* p, const float* g, float* img, int 
 {
     dim3 grid((p->N + T2 - 1) / T2, p->N >> LOGR2, count);
     Pass2Args a{g, img, p->N, p->n1};
-    pass2_kernel<LOGR2, T2, HORIZ><<<grid, kNT2, pass2_smem<LOGR2, T2, HORIZ>(), st>>>(a);
+    pass2_kernel<LOGR2, T2, HORIZ><<<grid, kNT2, pass2_smem<LOGR2, T2>(), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -627,12 +729,12 @@ cudaError_t set_p2_attr()
 {
     return cudaFuncSetAttribute(pass2_kernel<LOGR2, T2, HORIZ>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pass2_smem<LOGR2, T2, HORIZ>());
+                                (int)pass2_smem<LOGR2, T2>());
 }
 
-// Second-pass tile: T2 intercepts plus the 2^n2 halo fill exactly two 128-column chunks.
+// Second-pass tile: T2 intercepts plus the 2^n2 halo fit the two 128-column chunks.
 template <int LOGR2>
-constexpr int pass2_tile() { return 256 - (1 << LOGR2); }
+constexpr int pass2_tile() { return tile_width<(1 << LOGR2)>(); }
 
 template <int LOGR2, bool HORIZ>
 cudaError_t launch_pass2_n(const fbp_plan_s* p, const float* g, float* img, int count,
