@@ -31,7 +31,11 @@ const TableEntry kTable[] = {
 
 constexpr int kDefaultOrder = 3;
 constexpr size_t kAlign = 256;
-constexpr size_t kL2Budget = (size_t)96 << 20;   // bytes of filtered sinogram + G per chunk
+#ifndef FBP_L2_BUDGET_MB
+#define FBP_L2_BUDGET_MB 96
+#endif
+// bytes of filtered sinogram + G per chunk (sized to stay in L2 between kernels)
+constexpr size_t kL2Budget = (size_t)FBP_L2_BUDGET_MB << 20;
 constexpr size_t kMaxChunk = 4096;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
