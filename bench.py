@@ -52,6 +52,7 @@ def parse_args(argv=None):
     ap.add_argument("--slices", type=int, default=64, help="slices per GPU per step")
     ap.add_argument("--order", type=int, default=3, help="recursive filter order Q = Mb")
     ap.add_argument("--direct-slices", type=int, default=2)
+    ap.add_argument("--chunk", type=int, default=0, help="slices per launch (0 = library default)")
     ap.add_argument("--sample-pixels", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
@@ -203,14 +204,15 @@ def cpu_cores() -> int:
 
 
 # ----------------------------------------------------------------------------- traffic
-def traffic_for(kernel: str):
+def traffic_for(kernel: str, slices_per_launch: int):
     """ncu DRAM bytes per launch recorded in profiles/traffic.json for `kernel`, or None if
-    absent or if the kernel source changed since the counters were taken."""
+    absent, taken at another number of slices per launch, or if the kernel source changed
+    since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     rec = json.load(open(path)).get(kernel)
-    if not rec:
+    if not rec or rec.get("slices_per_launch") != slices_per_launch:
         return None
     src = os.path.join(ROOT, "paper_2007_06289_gb300", "csrc", rec["source"])
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -248,6 +250,8 @@ def run_ours(args):
         sino[j] = phantoms.ellipse_sinogram_torch(phantoms.random_ellipses(sd), N, K, M, dev,
                                                   I0, sd * 7919 + 1).float()
     plan = fbp.fbp_plan(N, K, M, S, (list(b), list(a)))
+    if args.chunk:
+        fbp.fbp_set_chunk(plan, args.chunk)
     img = torch.empty(plan.img_shape, device=dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -283,7 +287,9 @@ def run_ours(args):
     h_img = torch.empty(plan.img_shape, dtype=torch.float32, pin_memory=True)
     fbp.fbp_reconstruct_host(plan, h_sino, h_img)
     torch.cuda.synchronize(dev)
-    e2e_steps = max(1, min(args.steps, 5))
+    fbp.fbp_reconstruct_host(plan, h_sino, h_img)
+    torch.cuda.synchronize(dev)
+    e2e_steps = max(1, min(args.steps, 10))
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     for _ in range(e2e_steps):
@@ -336,7 +342,7 @@ def run_ours(args):
     dk = kern[dom]
     achieved = dk["bytes_per_launch"] / (dk["ms_per_launch"] / 1e3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
-                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic_for(dom),
+                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic_for(dom, plan.chunk),
                 "peak_source": peak_src,
                 "kernels": {k: {"ms_per_launch": round(v["ms_per_launch"], 5),
                                 "launches": v["launches"],

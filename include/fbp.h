@@ -92,6 +92,14 @@ fbp_status fbp_plan_destroy(fbp_plan_t plan);
  * fbp_reconstruct_host and fbp_direct_reconstruct need (0 if plan == NULL). */
 size_t fbp_workspace_bytes(fbp_plan_t plan);
 
+/* Slices per kernel sequence (1 .. batch, at most 4096; 0 restores the default: 16 slices,
+ * fewer where their first-pass buffers would pass 4 GiB).  Every launch of the fused
+ * pipeline then covers `chunk` slices (fbp_reconstruct_host stages at most 2 slices per
+ * copy); results do not depend on it, bit for bit.  Changes fbp_workspace_bytes, so it must
+ * come before the plan has a workspace.  No counterpart in the paper (an execution knob).
+ * Errors: FBP_ERR_INVALID_ARG (NULL plan, chunk out of range, workspace already present). */
+fbp_status fbp_set_chunk(fbp_plan_t plan, int chunk);
+
 /* Hand the plan a caller-owned device workspace of at least fbp_workspace_bytes bytes
  * (16-byte aligned).  Without one the plan allocates its own on first use (cudaMalloc),
  * which must then not happen inside a CUDA graph capture.  d_ws == NULL drops a caller

@@ -52,6 +52,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "fbp_plan_destroy": (I, [P]),
         "fbp_workspace_bytes": (S, [P]),
         "fbp_set_workspace": (I, [P, V, S]),
+        "fbp_set_chunk": (I, [P, I]),
         "fbp_filter_iir": (I, [P, V, V, V]),
         "fbp_resample_st": (I, [P, V, V, V]),
         "fbp_fht_backproject": (I, [P, V, V, V]),
@@ -146,10 +147,14 @@ class Plan:
         _check("fbp_plan", lib.fbp_plan(ctypes.byref(h), N, K, M, batch, cs, fuse_k))
         self._h = h
         self.N, self.K, self.M, self.batch = N, K, M, batch
-        vals = [ctypes.c_int() for _ in range(6)]
-        _check("fbp_plan_info", lib.fbp_plan_info(h, *[ctypes.byref(v) for v in vals]))
-        self.fuse_k, self.chunk = vals[4].value, vals[5].value
+        self._refresh()
         self._ws = None
+
+    def _refresh(self):
+        vals = [ctypes.c_int() for _ in range(6)]
+        _check("fbp_plan_info",
+               load_library().fbp_plan_info(self._h, *[ctypes.byref(v) for v in vals]))
+        self.fuse_k, self.chunk = vals[4].value, vals[5].value
 
     @property
     def handle(self):
@@ -190,6 +195,12 @@ def fbp_plan_destroy(plan: Plan) -> None:
 
 def fbp_workspace_bytes(plan: Plan) -> int:
     return int(load_library().fbp_workspace_bytes(plan.handle))
+
+
+def fbp_set_chunk(plan: Plan, chunk: int) -> None:
+    """Slices per kernel sequence (0 = default); before the plan has a workspace."""
+    _check("fbp_set_chunk", load_library().fbp_set_chunk(plan.handle, int(chunk)))
+    plan._refresh()
 
 
 def fbp_set_workspace(plan: Plan, ws) -> None:

@@ -49,6 +49,7 @@ def test_plan_rejects_bad_arguments_before_cuda(fbp):
     assert _plan_status(fbp, 64, 8, 8, 1, repeated) == 2        # repeated pole
     assert _plan_status(fbp, 64, 8, 8, 1, good, fuse_k=7) == 2  # fuse_k out of range
     assert _plan_status(fbp, 4096, 8, 8, 1, good, fuse_k=5) == 2   # second pass > 6 stages
+    assert _plan_status(fbp, 64, 8, 8, 1, good, fuse_k=1) == 2     # 2-row first-pass blocks
 
 
 def test_null_pointers_are_rejected(fbp):
@@ -57,5 +58,6 @@ def test_null_pointers_are_rejected(fbp):
     assert lib.fbp_reconstruct(None, None, None, None) == 1
     assert lib.fbp_filter_iir(None, None, None, None) == 1
     assert lib.fbp_workspace_bytes(None) == 0
+    assert lib.fbp_set_chunk(None, 1) == 1
     assert lib.fbp_plan_destroy(None) == 0
     assert lib.fbp_default_coeffs(256, 3, None) == 1

@@ -235,13 +235,16 @@ def test_pipeline_matches_fp64_oracle_at_full_size(fbp, torch, coeff_table):
 
 
 def test_chunked_batch_and_host_api(fbp, torch, coeff_table):
-    # N = 1024 processes two slices per chunk: a batch of 5 ends with a ragged chunk.
+    # Chunks of 4 slices: a batch of 5 ends with a ragged chunk (and the host path, which
+    # stages 2 slices per copy, with a ragged stage).
     N, B = 1024, 5
     K, M = phantoms.geometry_for(N)
     sino = phantoms.phantom_stack_torch(N, B, 40, "cuda", noise_i0=1e5)
     co = coeffs(coeff_table, N, 3)
     plan = fbp.fbp_plan(N, K, M, B, co)
-    assert plan.chunk < B
+    assert plan.chunk == B                          # default: the whole batch of 5
+    fbp.fbp_set_chunk(plan, 4)
+    assert plan.chunk == 4
     img = torch.empty(plan.img_shape, device="cuda")
     fbp.fbp_reconstruct(plan, sino, img)
     single = fbp.fbp_plan(N, K, M, 1, co)
@@ -255,6 +258,19 @@ def test_chunked_batch_and_host_api(fbp, torch, coeff_table):
         torch.cuda.synchronize()
         assert torch.equal(one[0], img[b])
     assert torch.equal(hi, img.cpu())
+    # every chunk size gives the same bits
+    for chunk in (1, 2, 3, 5):
+        p2 = fbp.fbp_plan(N, K, M, B, co)
+        fbp.fbp_set_chunk(p2, chunk)
+        assert p2.chunk == chunk
+        img2 = torch.empty(plan.img_shape, device="cuda")
+        fbp.fbp_reconstruct(p2, sino, img2)
+        torch.cuda.synchronize()
+        assert torch.equal(img2, img)
+    with pytest.raises(fbp.FbpError):
+        fbp.fbp_set_chunk(plan, 2)                  # the plan already has its workspace
+    with pytest.raises(fbp.FbpError):
+        fbp.fbp_set_chunk(fbp.fbp_plan(N, K, M, B, co), B + 1)
 
 
 def test_linearity(fbp, torch, coeff_table):
