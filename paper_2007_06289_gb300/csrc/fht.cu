@@ -36,7 +36,7 @@
 namespace fbp {
 namespace {
 
-constexpr int kWB1 = 256;      // pass-1 tile width including the halo of 2^n1 columns
+constexpr int kWB1 = 384;      // pass-1 tile width including the halo of 2^n1 columns
 constexpr int kNT1 = 512;      // pass-1 threads
 constexpr int kNT2 = 256;      // pass-2 threads
 constexpr int kWB2 = 256;      // pass-2 row width: tile plus halo
@@ -159,6 +159,10 @@ __device__ __forceinline__ void round_r2(float* buf, int warp, int lane, const S
     for (int pr = warp; pr < R / 2; pr += NWARPS) {
         float* A = buf + (2 * pr) * PITCH + 4 * lane;
         float* B = A + PITCH;
+        if constexpr (!std::is_same<Sink, SmemSink>::value) {
+            sink.begin(0, 2 * pr);
+            sink.begin(1, 2 * pr + 1);
+        }
 #pragma unroll
         for (int xb = 0; xb < WB; xb += 128) {
             float a[4], b[5];
@@ -197,7 +201,13 @@ __device__ __forceinline__ void quad_r4(float* A, float* B, float* C, float* D, 
     const float* Bw = B + tb;
     const float* Cw = C + 2 * tb + cb;
     const float* Dw = D + 3 * tb + db;
-#pragma unroll
+    if constexpr (!std::is_same<Sink, SmemSink>::value) {
+        sink.begin(0, a);
+        sink.begin(1, a + h);
+        sink.begin(2, a + 2 * h);
+        sink.begin(3, a + 3 * h);
+    }
+#pragma unroll 1
     for (int xb = 0; xb < WB; xb += 128) {
         float va[4], wb[8], wc[8], wd[12];
         ld4(va, A + xb);
@@ -313,10 +323,10 @@ constexpr int pass2_floats()
     return rows + (rows > T2 * (R + 1) ? rows : T2 * (R + 1));
 }
 
-// Tile width of a pass (columns it outputs): the 256-column row minus a halo of at least the
+// Tile width of a pass (columns it outputs): the WB-column row minus a halo of at least the
 // block's slope count, a multiple of 4 so that tiles start on 16-byte words.
-template <int R>
-constexpr int tile_width() { return 256 - (R > 4 ? R : 4); }
+template <int R, int WB>
+constexpr int tile_width() { return WB - (R > 4 ? R : 4); }
 
 // ------------------------------------------------------------------------ pass 1
 // G row layout.  Pass-1 row (block bi, slope tau) holds logical column v at storage index
@@ -335,7 +345,19 @@ struct GShiftSink {
     float* rows;            // storage offset 0 of G row 0 of this (slice, quarter, block) tile
     int W, T, c0, N, bi, logr, lane;
     mutable float carry[4][3];
-    __device__ __forceinline__ void operator()(int slot, int j, int x0, const float (&o)[4]) const
+    // per slot: the G row, its shift and the end of its stored offsets, set by begin()
+    mutable float* dst[4];
+    mutable int sh[4], send[4];
+
+    __device__ __forceinline__ void begin(int slot, int j) const
+    {
+        const int tau = rev_bits(j, logr);
+        sh[slot] = g_shift(tau, bi);
+        send[slot] = min(T, N + (tau + 1) * bi - c0) + sh[slot];   // storage offsets [sh, send)
+        dst[slot] = rows + (size_t)tau * W;
+    }
+
+    __device__ __forceinline__ void operator()(int slot, int, int x0, const float (&o)[4]) const
     {
         const int src_lane = (lane + 31) & 31;
         const float r1 = __shfl_sync(kFull, o[1], src_lane);
@@ -347,24 +369,22 @@ struct GShiftSink {
         carry[slot][0] = r1;
         carry[slot][1] = r2;
         carry[slot][2] = r3;
-        const int tau = rev_bits(j, logr);
-        const int sh = g_shift(tau, bi);
-        const int send = min(T, N + (tau + 1) * bi - c0) + sh;   // storage offsets [sh, send)
-        if (x0 >= send) return;
+        const int lo = sh[slot], hi = send[slot];
+        if (x0 >= hi) return;
+        float* d = dst[slot] + x0;
         float v[4];
-        switch (sh) {                                  // the same for the whole warp
+        switch (lo) {                                  // the same for the whole warp
             case 0: v[0] = o[0]; v[1] = o[1]; v[2] = o[2]; v[3] = o[3]; break;
             case 1: v[0] = p3; v[1] = o[0]; v[2] = o[1]; v[3] = o[2]; break;
             case 2: v[0] = p2; v[1] = p3; v[2] = o[0]; v[3] = o[1]; break;
             default: v[0] = p1; v[1] = p2; v[2] = p3; v[3] = o[0]; break;
         }
-        float* dst = rows + (size_t)tau * W + x0;
-        if (x0 >= sh && x0 + 4 <= send) {
-            st4(dst, v);
+        if (x0 >= lo && x0 + 4 <= hi) {
+            st4(d, v);
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if (x0 + k >= sh && x0 + k < send) dst[k] = v[k];
+                if (x0 + k >= lo && x0 + k < hi) d[k] = v[k];
         }
     }
 };
@@ -422,7 +442,7 @@ pass1_kernel(Pass1Args a)
 {
     constexpr int R = 1 << LOGR;
     constexpr int WB = kWB1;
-    constexpr int T = tile_width<R>();
+    constexpr int T = tile_width<R, WB>();
     constexpr int PITCH = hough_pitch<R, WB>();
     constexpr int NWARPS = kNT1 / 32;
     extern __shared__ __align__(16) float buf[];
@@ -698,7 +718,7 @@ cudaError_t launch_pass1_t(const fbp_plan_s* p, const float* src, float* g, int 
                            cudaStream_t st)
 {
     constexpr int R = 1 << LOGR;
-    constexpr int T = tile_width<R>();
+    constexpr int T = tile_width<R, kWB1>();
     const int nblocks = p->N >> LOGR;
     const int max_cols = p->N + R * (nblocks - 1);
     dim3 grid((max_cols + T - 1) / T, 4 * nblocks, count);
@@ -734,7 +754,7 @@ cudaError_t set_p2_attr()
 
 // Second-pass tile: T2 intercepts plus the 2^n2 halo fit the two 128-column chunks.
 template <int LOGR2>
-constexpr int pass2_tile() { return tile_width<(1 << LOGR2)>(); }
+constexpr int pass2_tile() { return tile_width<(1 << LOGR2), kWB2>(); }
 
 template <int LOGR2, bool HORIZ>
 cudaError_t launch_pass2_n(const fbp_plan_s* p, const float* g, float* img, int count,
