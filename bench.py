@@ -55,6 +55,10 @@ def parse_args(argv=None):
     ap.add_argument("--chunk", type=int, default=0, help="slices per launch (0 = library default)")
     ap.add_argument("--sample-pixels", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=("stack", "ragged"), default="stack",
+                    help="stack: the N = 2048 64-slice stack (default); ragged: a volume of "
+                         "--ragged-slices slices with N drawn uniformly from 256..2048")
+    ap.add_argument("--ragged-slices", type=int, default=512)
     return ap.parse_args(argv)
 
 
@@ -459,10 +463,96 @@ def run_reference(args):
     return line
 
 
+# ----------------------------------------------------------------------------- ragged volume
+RAGGED_SIZES = (256, 512, 1024, 2048)
+RAGGED_SEED = 2022
+RAGGED_DISTINCT = 4           # distinct phantoms per size, replicated over that size's slices
+
+
+def run_ragged(args):
+    """A volume of slices of mixed sizes in one fbp_volume_run (graph-captured, autotuned
+    outside the timed region).  Slice i has N drawn uniformly from RAGGED_SIZES with seed
+    RAGGED_SEED; each size's slices cycle through RAGGED_DISTINCT seeded noisy phantoms
+    (every slice in its own buffers).  One step = one run over the whole volume."""
+    import numpy as np
+    import torch
+
+    import phantoms
+    from paper_2007_06289_gb300 import binding as fbp
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(RAGGED_SEED + rank)
+    sizes = rng.choice(RAGGED_SIZES, size=args.ragged_slices)
+    proto = {}
+    for N in RAGGED_SIZES:
+        proto[N] = phantoms.phantom_stack_torch(int(N), RAGGED_DISTINCT, RAGGED_SEED * 10 + N,
+                                                dev, noise_i0=I0)
+    items, seen = [], {N: 0 for N in RAGGED_SIZES}
+    for N in sizes:
+        N = int(N)
+        sino = proto[N][seen[N] % RAGGED_DISTINCT].clone()
+        seen[N] += 1
+        items.append((N, sino, torch.empty((N, N), device=dev)))
+    stream = torch.cuda.Stream(dev)
+    vol = fbp.fbp_volume_create(items, order=args.order, graph=True)
+    choices = vol.tune(stream)
+    for _ in range(max(3, args.warmup)):
+        vol.run(stream)
+    stream.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        vol.run(stream)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, world, dev)
+    groups = [vol.group(g) for g in range(vol.info()["groups"])]
+    total = args.ragged_slices * world
+    voxels = sum(int(N) * int(N) for N in sizes) * world
+    line = {"metric": "slices/s of a ragged volume (N uniform in {256,512,1024,2048})",
+            "value": round(total / (ms / 1e3), 2), "unit": "slices/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": f"synthetic: {RAGGED_DISTINCT} seeded noisy ellipse phantoms per size, "
+                    "replicated; every slice in its own buffers",
+            "config": {"workload": f"ragged volume of {args.ragged_slices} slices per GPU",
+                       "slices_per_size": {str(N): int((sizes == N).sum()) for N in RAGGED_SIZES},
+                       "graph": True,
+                       "groups": [{k: g[k] for k in ("N", "items", "fuse_k", "chunk")}
+                                  for g in groups],
+                       "l2": "no flush: the volume's sinograms (GBs) exceed L2"},
+            "voxels_per_s": round(voxels / (ms / 1e3), 1),
+            "tuned": [list(c) for c in choices],
+            "clocks": clocks,
+            "gpu_launches": args.steps * sum(
+                -(-g["items"] // g["chunk"]) * (4 if g["N"] > 64 else 3) for g in groups)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ragged":
+        run_ragged(args)
     else:
         run_ours(args)
 

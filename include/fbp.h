@@ -136,6 +136,55 @@ fbp_status fbp_reconstruct(fbp_plan_t plan, const float* d_sino, float* d_img, v
 fbp_status fbp_reconstruct_host(fbp_plan_t plan, const float* h_sino, float* h_img, int count,
                                 void* stream);
 
+/* ------------------------------------------------------------------ ragged volumes
+ * A volume whose slices differ in size (N, K, M), each slice in its own buffers.  No
+ * counterpart in the paper (which reconstructs one slice at a time); an execution layer
+ * over the same pipeline. */
+typedef struct {
+    int N, K, M;            /* image size (power of two, 2..4096), angles, detector bins */
+    const float* d_sino;    /* device [K][M], 16-byte aligned, caller-owned */
+    float* d_img;           /* device [N][N], 16-byte aligned, caller-owned */
+} fbp_item;
+
+typedef struct fbp_volume_s* fbp_volume_t;
+
+enum { FBP_VOLUME_GRAPH = 1 };  /* capture the whole volume into a CUDA graph, replay it */
+
+/* Executor for `count` items: items are grouped by (N, K, M); each group gets a plan with
+ * the built-in coefficients of its N (order `order`, 0 = default), device tables of its
+ * items' pointers, a workspace and a stream.  All device memory is allocated here.
+ * fbp_volume_run then reconstructs every item (each image bit-identical to reconstructing
+ * that slice alone with fbp_reconstruct).  The item array is copied; the buffers it points
+ * to must stay valid while the volume is used.
+ * Errors: FBP_ERR_INVALID_ARG (NULL, count < 1, K or M < 2, unknown flags),
+ * FBP_ERR_MISALIGNED, FBP_ERR_UNSUPPORTED (N), FBP_ERR_OOM, FBP_ERR_CUDA. */
+fbp_status fbp_volume_create(fbp_volume_t* out, const fbp_item* items, int count, int order,
+                             int flags);
+
+/* Reconstruct every item, asynchronously on `stream` (the groups run on internal streams
+ * forked from and joined back into `stream`).  With FBP_VOLUME_GRAPH the first call
+ * captures the work into a CUDA graph and every call launches that graph; `stream` must
+ * then be a created stream (not the legacy or per-thread default: FBP_ERR_INVALID_ARG). */
+fbp_status fbp_volume_run(fbp_volume_t v, void* stream);
+
+/* Autotuner: for every group, times the supported first-pass fusion depths and 1, 2, 4, 8,
+ * 16 slices per launch (up to the group's size) on the volume's own items, on `stream`,
+ * and keeps the fastest pair.  Synchronous.  Overwrites the items' images (with the same
+ * bits every choice gives).  fuse_k_out / chunk_out (optional, [groups]) receive the
+ * choices.  A captured graph is dropped and re-captured by the next run. */
+fbp_status fbp_volume_tune(fbp_volume_t v, void* stream, int* fuse_k_out, int* chunk_out);
+
+/* Number of groups and the total workspace bytes of their plans. */
+fbp_status fbp_volume_info(fbp_volume_t v, int* groups, size_t* workspace_bytes);
+
+/* Shape, item count, fusion depth and slices per launch of group `group` (groups are
+ * numbered in order of their first item). */
+fbp_status fbp_volume_group(fbp_volume_t v, int group, int* N, int* K, int* M, int* items,
+                            int* fuse_k, int* chunk);
+
+/* Free everything the volume owns (waits for the device first).  NULL is a no-op. */
+fbp_status fbp_volume_destroy(fbp_volume_t v);
+
 /* Allocation-free variant of fbp_fht_backproject, for callers that cannot allocate device
  * memory (code running inside another framework's memory pool, plugins handed only their
  * input and output buffers, real-time loops where an allocation may stall or fail): it

@@ -27,6 +27,14 @@ class FbpError(RuntimeError):
         super().__init__(f"{fn} failed: {_STATUS.get(code, code)} ({fbp_status_str(code)})")
 
 
+class fbp_item(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("K", ctypes.c_int), ("M", ctypes.c_int),
+                ("d_sino", ctypes.c_void_p), ("d_img", ctypes.c_void_p)]
+
+
+FBP_VOLUME_GRAPH = 1
+
+
 class fbp_iir_coeffs(ctypes.Structure):
     _fields_ = [("mb", ctypes.c_int), ("q", ctypes.c_int),
                 ("b", ctypes.c_double * MAX_ORDER), ("a", ctypes.c_double * MAX_ORDER)]
@@ -66,6 +74,12 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "fbp_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_longlong)]),
         "fbp_status_str": (ctypes.c_char_p, [I]),
+        "fbp_volume_create": (I, [ctypes.POINTER(P), ctypes.POINTER(fbp_item), I, I, I]),
+        "fbp_volume_run": (I, [P, V]),
+        "fbp_volume_tune": (I, [P, V, ctypes.POINTER(I), ctypes.POINTER(I)]),
+        "fbp_volume_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(S)]),
+        "fbp_volume_group": (I, [P, I] + [ctypes.POINTER(I)] * 6),
+        "fbp_volume_destroy": (I, [P]),
         "fbp_last_device_error": (I, [P]),
     }
     for name, (res, args) in sig.items():
@@ -300,3 +314,88 @@ def fbp_profile_read(plan: Plan) -> dict:
 
 def fbp_last_device_error(plan: Plan) -> int:
     return int(load_library().fbp_last_device_error(plan.handle))
+
+
+# ----------------------------------------------------------------------------- ragged volumes
+class Volume:
+    """Owner of an fbp_volume_t over slices of mixed sizes: `items` is a list of
+    (N, sino, img) with sino a [K][M] and img an [N][N] float32 CUDA tensor (kept alive by
+    the volume)."""
+
+    def __init__(self, items, order: int = 0, graph: bool = False):
+        lib = load_library()
+        arr = (fbp_item * len(items))()
+        for i, (N, sino, img) in enumerate(items):
+            if sino.dim() != 2 or tuple(img.shape) != (N, N):
+                raise ValueError(f"item {i}: expected sino [K][M] and img [N][N]")
+            K, M = sino.shape
+            arr[i] = fbp_item(N, K, M, _dev_ptr(sino, (K, M), "sino"),
+                              _dev_ptr(img, (N, N), "img"))
+        h = ctypes.c_void_p()
+        _check("fbp_volume_create",
+               lib.fbp_volume_create(ctypes.byref(h), arr, len(items), int(order),
+                                     FBP_VOLUME_GRAPH if graph else 0))
+        self._h = h
+        self._items = list(items)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def run(self, stream=None) -> None:
+        _check("fbp_volume_run", load_library().fbp_volume_run(self._h, _stream_ptr(stream)))
+
+    def tune(self, stream=None) -> list[tuple[int, int]]:
+        """Autotune every group; returns [(fuse_k, chunk)] per group."""
+        n = self.info()["groups"]
+        ks, cs = (ctypes.c_int * n)(), (ctypes.c_int * n)()
+        _check("fbp_volume_tune",
+               load_library().fbp_volume_tune(self._h, _stream_ptr(stream), ks, cs))
+        return [(ks[i], cs[i]) for i in range(n)]
+
+    def info(self) -> dict:
+        g, ws = ctypes.c_int(), ctypes.c_size_t()
+        _check("fbp_volume_info",
+               load_library().fbp_volume_info(self._h, ctypes.byref(g), ctypes.byref(ws)))
+        return {"groups": g.value, "workspace_bytes": ws.value}
+
+    def group(self, i: int) -> dict:
+        vals = [ctypes.c_int() for _ in range(6)]
+        _check("fbp_volume_group", load_library().fbp_volume_group(
+            self._h, int(i), *[ctypes.byref(v) for v in vals]))
+        return dict(zip(("N", "K", "M", "items", "fuse_k", "chunk"), (v.value for v in vals)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().fbp_volume_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fbp_volume_create(items, order: int = 0, graph: bool = False) -> Volume:
+    return Volume(items, order, graph)
+
+
+def fbp_volume_run(volume: Volume, stream=None) -> None:
+    volume.run(stream)
+
+
+def fbp_volume_tune(volume: Volume, stream=None):
+    return volume.tune(stream)
+
+
+def fbp_volume_info(volume: Volume) -> dict:
+    return volume.info()
+
+
+def fbp_volume_group(volume: Volume, i: int) -> dict:
+    return volume.group(i)
+
+
+def fbp_volume_destroy(volume: Volume) -> None:
+    volume.close()

@@ -304,52 +304,6 @@ int ilog2(int v)
     return n;
 }
 
-// Slices per kernel sequence.  Larger chunks give every launch a larger grid (fewer
-// partial waves, fewer dependent-launch gaps) at the price of a working set that no longer
-// stays in L2; the kernels are not DRAM-bound, so the grid size wins (measured on GB300 at
-// N = 2048, slices/s for 1, 2, 4, 8, 16 slices per launch: 5590, 6456, 7062, 7459, 7670).
-int default_chunk(const fbp_plan_s* p)
-{
-    size_t chunk = kChunkSlices;
-    const size_t g_bytes = fbp::lin_floats(p) * sizeof(float);
-    if (chunk * g_bytes > kChunkBytes) chunk = kChunkBytes / g_bytes;
-    if (chunk < 1) chunk = 1;
-    if (chunk > (size_t)p->batch) chunk = p->batch;
-    return (int)chunk;
-}
-
-// Workspace offsets for `chunk` slices per kernel sequence: filtered sinogram (guarded
-// rows), first-pass buffer G, and two staging slots each for the host pipeline.
-void layout_workspace(fbp_plan_s* p, int chunk)
-{
-    const size_t s_bytes = fbp::sino_floats(p) * sizeof(float);
-    const size_t f_bytes = (size_t)p->K * fbp::filt_pitch(p) * sizeof(float);
-    const size_t g_bytes = fbp::lin_floats(p) * sizeof(float);
-    p->chunk = chunk;
-    size_t off = 0;
-    p->off_filt = off; off = align_up(off + chunk * f_bytes);
-    p->off_g = off; off = align_up(off + chunk * g_bytes);
-    for (int b = 0; b < 2; ++b) { p->off_stage_sino[b] = off; off = align_up(off + chunk * s_bytes); }
-    for (int b = 0; b < 2; ++b) {
-        p->off_stage_img[b] = off;
-        off = align_up(off + chunk * fbp::img_floats(p) * sizeof(float));
-    }
-    p->ws_bytes = off;
-}
-
-fbp_status ensure_workspace(fbp_plan_s* p)
-{
-    if (p->ws) return FBP_OK;
-    void* ws = nullptr;
-    if (cudaMalloc(&ws, p->ws_bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return FBP_ERR_OOM;
-    }
-    p->ws = ws;
-    p->ws_owned = 1;
-    return FBP_OK;
-}
-
 float* ws_ptr(const fbp_plan_s* p, size_t off) { return (float*)((char*)p->ws + off); }
 
 cudaEvent_t prof_event(fbp_plan_s* p)
@@ -407,25 +361,82 @@ cudaError_t prof_collect(fbp_plan_s* p)
     return err;
 }
 
+}  // namespace
+
+namespace fbp {
+
+// Slices per kernel sequence.  Larger chunks give every launch a larger grid (fewer
+// partial waves, fewer dependent-launch gaps) at the price of a working set that no longer
+// stays in L2; the kernels are not DRAM-bound, so the grid size wins (measured on GB300 at
+// N = 2048, slices/s for 1, 2, 4, 8, 16 slices per launch: 5590, 6456, 7062, 7459, 7670).
+int default_chunk(const fbp_plan_s* p)
+{
+    size_t chunk = kChunkSlices;
+    const size_t g_bytes = fbp::lin_floats(p) * sizeof(float);
+    if (chunk * g_bytes > kChunkBytes) chunk = kChunkBytes / g_bytes;
+    if (chunk < 1) chunk = 1;
+    if (chunk > (size_t)p->batch) chunk = p->batch;
+    return (int)chunk;
+}
+
+// Workspace offsets for `chunk` slices per kernel sequence: filtered sinogram (guarded
+// rows), first-pass buffer G, and two staging slots each for the host pipeline.
+void layout_workspace(fbp_plan_s* p, int chunk)
+{
+    const size_t s_bytes = fbp::sino_floats(p) * sizeof(float);
+    const size_t f_bytes = (size_t)p->K * fbp::filt_pitch(p) * sizeof(float);
+    const size_t g_bytes = fbp::lin_floats(p) * sizeof(float);
+    p->chunk = chunk;
+    size_t off = 0;
+    p->off_filt = off; off = align_up(off + chunk * f_bytes);
+    p->off_g = off; off = align_up(off + chunk * g_bytes);
+    for (int b = 0; b < 2; ++b) { p->off_stage_sino[b] = off; off = align_up(off + chunk * s_bytes); }
+    for (int b = 0; b < 2; ++b) {
+        p->off_stage_img[b] = off;
+        off = align_up(off + chunk * fbp::img_floats(p) * sizeof(float));
+    }
+    p->ws_bytes = off;
+}
+
+fbp_status ensure_workspace(fbp_plan_s* p)
+{
+    if (p->ws) return FBP_OK;
+    void* ws = nullptr;
+    if (cudaMalloc(&ws, p->ws_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return FBP_ERR_OOM;
+    }
+    p->ws = ws;
+    p->ws_owned = 1;
+    return FBP_OK;
+}
+
 // One chunk of the fused pipeline: filter -> (resample + pass 1) -> (pass 2 + sum).
 cudaError_t reconstruct_chunk(fbp_plan_s* p, const float* sino, float* img, int cnt,
-                              cudaStream_t st)
+                              cudaStream_t st, const float* const* sino_tab, float* const* img_tab)
 {
     float* filt = ws_ptr(p, p->off_filt);
     float* g = ws_ptr(p, p->off_g);
     cudaError_t e = run(p, FBP_KERNEL_IIR, st,
-                        [&] { return fbp::launch_iir(p, sino, filt, cnt * p->K, fbp::filt_pitch(p), st); });
+                        [&] { return launch_iir(p, sino, filt, cnt * p->K, filt_pitch(p), st, sino_tab); });
     if (e == cudaSuccess)
         e = run(p, FBP_KERNEL_PASS1_RESAMPLE, st,
-                [&] { return fbp::launch_pass1(p, filt, false, g, cnt, st); });
+                [&] { return launch_pass1(p, filt, false, g, cnt, st); });
     if (e == cudaSuccess)
-        e = run(p, FBP_KERNEL_PASS2, st, [&] { return fbp::launch_pass2(p, g, img, cnt, false, st); });
+        e = run(p, FBP_KERNEL_PASS2, st,
+                [&] { return launch_pass2(p, g, img, cnt, false, st, img_tab); });
     if (e == cudaSuccess && p->n2 > 0)
-        e = run(p, FBP_KERNEL_PASS2_H, st, [&] { return fbp::launch_pass2(p, g, img, cnt, true, st); });
+        e = run(p, FBP_KERNEL_PASS2_H, st,
+                [&] { return launch_pass2(p, g, img, cnt, true, st, img_tab); });
     return e;
 }
 
-}  // namespace
+}  // namespace fbp
+
+using fbp::default_chunk;
+using fbp::ensure_workspace;
+using fbp::layout_workspace;
+using fbp::reconstruct_chunk;
 
 extern "C" {
 

@@ -88,16 +88,18 @@ namespace fbp {
 // Kernel launchers (each returns cudaGetLastError() after the launch).
 // out_pitch >= M: output rows are out_pitch floats apart, the M samples centred in each
 // with (out_pitch - M) / 2 zeros before them and the rest after (guard bins).
+// in_tab (device array, optional): slice s of the input is in_tab[s] instead of in + s K M.
 cudaError_t launch_iir(const fbp_plan_s* p, const float* in, float* out, int rows,
-                       int out_pitch, cudaStream_t st);
+                       int out_pitch, cudaStream_t st, const float* const* in_tab = nullptr);
 cudaError_t launch_resample(const fbp_plan_s* p, const float* filt, float* lin, int count,
                             cudaStream_t st);
 cudaError_t launch_pass1(const fbp_plan_s* p, const float* src, bool from_lin, float* g,
                          int count, cudaStream_t st);
 // Second pass: horizontal == false launches the v quarters (stores F_v- + F_v+),
 // horizontal == true the h quarters (adds F_h- + F_h+); the v launch must come first.
+// img_tab (device array, optional): slice s of the image is img_tab[s] instead of img + s N N.
 cudaError_t launch_pass2(const fbp_plan_s* p, const float* g, float* img, int count,
-                         bool horizontal, cudaStream_t st);
+                         bool horizontal, cudaStream_t st, float* const* img_tab = nullptr);
 cudaError_t launch_fir(const fbp_plan_s* p, const float* in, float* out, int rows,
                        cudaStream_t st);
 cudaError_t launch_direct_bp(const fbp_plan_s* p, const float* filt, float* img, int count,
@@ -107,6 +109,17 @@ cudaError_t launch_direct_bp(const fbp_plan_s* p, const float* filt, float* img,
 // every row, so resampling reads bins -kGuard .. M+kGuard-1 without range checks.
 constexpr int kGuard = 2;
 inline int filt_pitch(const fbp_plan_s* p) { return p->M + 2 * kGuard; }
+
+// Plan internals shared by the entry points (fbp_api.cu) and the ragged volume (volume.cu).
+int default_chunk(const fbp_plan_s* p);
+void layout_workspace(fbp_plan_s* p, int chunk);
+fbp_status ensure_workspace(fbp_plan_s* p);
+// The fused pipeline over cnt consecutive slices of one chunk on stream st: filter ->
+// (resample + pass 1) -> (pass 2 + sum).  sino_tab / img_tab (device arrays, optional)
+// give the slices' own sinogram / image buffers instead of sino + s K M / img + s N N.
+cudaError_t reconstruct_chunk(fbp_plan_s* p, const float* sino, float* img, int cnt,
+                              cudaStream_t st, const float* const* sino_tab = nullptr,
+                              float* const* img_tab = nullptr);
 
 inline size_t lin_floats(const fbp_plan_s* p) { return (size_t)4 * p->N * 2 * p->N; }
 inline size_t sino_floats(const fbp_plan_s* p) { return (size_t)p->K * p->M; }

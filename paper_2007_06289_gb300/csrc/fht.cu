@@ -535,6 +535,7 @@ pass1_kernel(Pass1Args a)
 struct Pass2Args {
     const float* g;         // [count][4][N][2N]
     float* img;             // [count][N][N]
+    float* const* img_tab;  // optional: slice s's image at img_tab[s]
     int N, n1;
 };
 
@@ -586,7 +587,7 @@ pass2_kernel(Pass2Args a)
     const int tau_hi = blockIdx.y;
     const int s = blockIdx.z;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* img = a.img + (size_t)s * N * N;
+    float* img = a.img_tab ? a.img_tab[s] : a.img + (size_t)s * N * N;
 
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
@@ -691,7 +692,7 @@ pass2_kernel(Pass2Args a)
 
 // Single-pass sizes (n <= 6): G already holds the quarter images H_q[tau][u]; sum them.
 __global__ void __launch_bounds__(256)
-combine_kernel(const float* __restrict__ g, float* __restrict__ img, int N)
+combine_kernel(const float* __restrict__ g, float* __restrict__ img, float* const* img_tab, int N)
 {
     const int W = 2 * N;
     const int s = blockIdx.y;
@@ -703,7 +704,7 @@ combine_kernel(const float* __restrict__ g, float* __restrict__ img, int N)
     const size_t qs = (size_t)N * W;
     const float v = h[(size_t)y * W + x] + h[qs + (size_t)y * W + (N - 1 - x)];
     const float hh = h[2 * qs + (size_t)x * W + y] + h[3 * qs + (size_t)x * W + (N - 1 - y)];
-    img[(size_t)s * N * N + p] = v + hh;
+    (img_tab ? img_tab[s] : img + (size_t)s * N * N)[p] = v + hh;
 }
 
 // ------------------------------------------------------------------------ launchers
@@ -729,10 +730,10 @@ cudaError_t launch_pass1_t(const fbp_plan_s* p, const float* src, float* g, int 
 
 template <int LOGR2, int T2, bool HORIZ>
 cudaError_t launch_pass2_t(const fbp_plan_s* p, const float* g, float* img, int count,
-                           cudaStream_t st)
+                           cudaStream_t st, float* const* img_tab)
 {
     dim3 grid((p->N + T2 - 1) / T2, p->N >> LOGR2, count);
-    Pass2Args a{g, img, p->N, p->n1};
+    Pass2Args a{g, img, img_tab, p->N, p->n1};
     pass2_kernel<LOGR2, T2, HORIZ><<<grid, kNT2, pass2_smem<LOGR2, T2>(), st>>>(a);
     return cudaGetLastError();
 }
@@ -758,9 +759,9 @@ constexpr int pass2_tile() { return tile_width<(1 << LOGR2), kWB2>(); }
 
 template <int LOGR2, bool HORIZ>
 cudaError_t launch_pass2_n(const fbp_plan_s* p, const float* g, float* img, int count,
-                           cudaStream_t st)
+                           cudaStream_t st, float* const* img_tab)
 {
-    return launch_pass2_t<LOGR2, pass2_tile<LOGR2>(), HORIZ>(p, g, img, count, st);
+    return launch_pass2_t<LOGR2, pass2_tile<LOGR2>(), HORIZ>(p, g, img, count, st, img_tab);
 }
 
 }  // namespace
@@ -805,19 +806,19 @@ cudaError_t launch_pass1(const fbp_plan_s* p, const float* src, bool from_lin, f
 }
 
 cudaError_t launch_pass2(const fbp_plan_s* p, const float* g, float* img, int count,
-                         bool horizontal, cudaStream_t st)
+                         bool horizontal, cudaStream_t st, float* const* img_tab)
 {
     if (count <= 0) return cudaSuccess;
     if (p->n2 == 0) {
         if (horizontal) return cudaSuccess;            // the sum kernel does all quarters
         dim3 grid((p->N * p->N + 255) / 256, count);
-        combine_kernel<<<grid, 256, 0, st>>>(g, img, p->N);
+        combine_kernel<<<grid, 256, 0, st>>>(g, img, img_tab, p->N);
         return cudaGetLastError();
     }
     switch (p->n2 * 2 + (horizontal ? 1 : 0)) {
 #define FBP_C(L)                                                              \
-    case 2 * L: return launch_pass2_n<L, false>(p, g, img, count, st);       \
-    case 2 * L + 1: return launch_pass2_n<L, true>(p, g, img, count, st);
+    case 2 * L: return launch_pass2_n<L, false>(p, g, img, count, st, img_tab);       \
+    case 2 * L + 1: return launch_pass2_n<L, true>(p, g, img, count, st, img_tab);
         FBP_C(1) FBP_C(2) FBP_C(3) FBP_C(4) FBP_C(5) FBP_C(6)
 #undef FBP_C
         default: return cudaErrorInvalidValue;

@@ -266,7 +266,7 @@ __device__ __forceinline__ void store_row(float* dst, const float* src, long lon
 // in may equal out (each CTA reads its rows completely before it writes them).
 template <int JR, int JC, bool TAPS, int LT>
 __global__ void __launch_bounds__(kIirThreads)
-iir_ramp_kernel(const float* in, float* out, int rows, int M,
+iir_ramp_kernel(const float* in, const float* const* in_tab, int K, float* out, int rows, int M,
                 int out_pitch, int rows_per_cta, IirParams prm)
 {
     constexpr int SF = state_floats<JR, JC>();
@@ -284,7 +284,15 @@ iir_ramp_kernel(const float* in, float* out, int rows, int M,
     const int rb = row_buffer_floats(M, wpr, L);
     // per row: staged input sp, result sz (each shifted to the global 16-byte phase of its
     // row), then the warp totals of both directions
-    const long long e_in = row * (long long)M;
+    // input row: in + row M, or row (row mod K) of slice table entry row / K (each entry a
+    // 16-byte-aligned [K][M] sinogram); e_in counts floats from a 16-byte-aligned base
+    const float* in_base = in;
+    long long e_in = row * (long long)M;
+    if (in_tab != nullptr && live) {
+        const long long sl = row / K;
+        in_base = in_tab[sl];
+        e_in = (row - sl * K) * (long long)M;
+    }
     const int lead = (out_pitch - M) / 2;
     const long long e_out = row * (long long)out_pitch + lead;
     float* sp = smem + (size_t)rloc * 2 * rb + (e_in & 3);
@@ -293,7 +301,7 @@ iir_ramp_kernel(const float* in, float* out, int rows, int M,
     const int span = nthr * L;
 
     if (live) {
-        load_row(sp, in + e_in, e_in, M, t, nthr);
+        load_row(sp, in_base + e_in, e_in, M, t, nthr);
         for (int n = M + t; n <= span; n += nthr) sp[n] = 0.0f;
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -379,7 +387,7 @@ iir_ramp_kernel(const float* in, float* out, int rows, int M,
 
 template <int JR, int JC, bool TAPS, int LT>
 cudaError_t launch_iir_t(const fbp_plan_s* p, const float* in, float* out, int rows,
-                         int out_pitch, cudaStream_t st)
+                         int out_pitch, cudaStream_t st, const float* const* in_tab)
 {
     constexpr int SF = state_floats<JR, JC>();
     const int wpr = p->iir.wpr;
@@ -389,8 +397,8 @@ cudaError_t launch_iir_t(const fbp_plan_s* p, const float* in, float* out, int r
     const size_t smem = ((size_t)rows_per_cta * 2 * rb + (size_t)rows_per_cta * 2 * wpr * SF) * sizeof(float);
     if (smem > (size_t)kMaxSmem || threads > 1024) return cudaErrorInvalidValue;
     const int grid = (rows + rows_per_cta - 1) / rows_per_cta;
-    iir_ramp_kernel<JR, JC, TAPS, LT><<<grid, threads, smem, st>>>(in, out, rows, p->M, out_pitch,
-                                                                   rows_per_cta, p->iir);
+    iir_ramp_kernel<JR, JC, TAPS, LT><<<grid, threads, smem, st>>>(
+        in, in_tab, p->K, out, rows, p->M, out_pitch, rows_per_cta, p->iir);
     return cudaGetLastError();
 }
 
@@ -428,15 +436,17 @@ cudaError_t prepare_iir_kernels()
 }
 
 cudaError_t launch_iir(const fbp_plan_s* p, const float* in, float* out, int rows,
-                       int out_pitch, cudaStream_t st)
+                       int out_pitch, cudaStream_t st, const float* const* in_tab)
 {
     if (rows <= 0) return cudaSuccess;
     const int jr = p->iir.jr, jc = p->iir.jc;
 #define FBP_X(R, C)                                                                   \
     if (jr == R && jc == C)                                                           \
-        return p->iir.nd > 0 ? launch_iir_t<R, C, true, 0>(p, in, out, rows, out_pitch, st)        \
-             : p->iir.L == kIirLmax ? launch_iir_t<R, C, false, kIirLmax>(p, in, out, rows, out_pitch, st) \
-                                    : launch_iir_t<R, C, false, 0>(p, in, out, rows, out_pitch, st);
+        return p->iir.nd > 0                                                                     \
+                   ? launch_iir_t<R, C, true, 0>(p, in, out, rows, out_pitch, st, in_tab)           \
+               : p->iir.L == kIirLmax                                                           \
+                   ? launch_iir_t<R, C, false, kIirLmax>(p, in, out, rows, out_pitch, st, in_tab)   \
+                   : launch_iir_t<R, C, false, 0>(p, in, out, rows, out_pitch, st, in_tab);
     FBP_IIR_MODES(FBP_X)
 #undef FBP_X
     return cudaErrorInvalidValue;

@@ -151,10 +151,14 @@ def ellipse_sinogram_torch(ellipses, N: int, K: int, M: int, device, noise_i0=No
     return p * (N / 2.0)
 
 
-def phantom_stack_torch(N: int, slices: int, base_seed: int, device, noise_i0=None):
-    """float32 [slices][K][M] stack on ``device``; slice i uses seed base_seed + i."""
+def phantom_stack_torch(N: int, slices: int, base_seed: int, device, noise_i0=None, K=None,
+                        M=None):
+    """float32 [slices][K][M] stack on ``device``; slice i uses seed base_seed + i.  K and M
+    default to geometry_for(N)."""
     import torch
-    K, M = geometry_for(N)
+    K0, M0 = geometry_for(N)
+    K = K0 if K is None else K
+    M = M0 if M is None else M
     out = torch.empty((slices, K, M), dtype=torch.float32, device=device)
     for i in range(slices):
         ell = random_ellipses(base_seed + i)

@@ -61,3 +61,28 @@ def test_null_pointers_are_rejected(fbp):
     assert lib.fbp_set_chunk(None, 1) == 1
     assert lib.fbp_plan_destroy(None) == 0
     assert lib.fbp_default_coeffs(256, 3, None) == 1
+
+
+def test_volume_arguments_are_checked_before_cuda(fbp):
+    lib = fbp.load_library()
+    h = ctypes.c_void_p()
+    item = fbp.fbp_item(64, 96, 91, 16 * 1000, 16 * 2000)     # aligned, never dereferenced
+    arr = (fbp.fbp_item * 1)(item)
+    assert lib.fbp_volume_create(None, arr, 1, 0, 0) == 1
+    assert lib.fbp_volume_create(ctypes.byref(h), None, 1, 0, 0) == 1
+    assert lib.fbp_volume_create(ctypes.byref(h), arr, 0, 0, 0) == 1
+    assert lib.fbp_volume_create(ctypes.byref(h), arr, 1, 0, 4) == 1         # unknown flag
+    bad = (fbp.fbp_item * 1)(fbp.fbp_item(96, 96, 91, 16 * 1000, 16 * 2000))
+    assert lib.fbp_volume_create(ctypes.byref(h), bad, 1, 0, 0) == 2         # N = 96
+    bad = (fbp.fbp_item * 1)(fbp.fbp_item(64, 1, 91, 16 * 1000, 16 * 2000))
+    assert lib.fbp_volume_create(ctypes.byref(h), bad, 1, 0, 0) == 1         # K = 1
+    bad = (fbp.fbp_item * 1)(fbp.fbp_item(64, 96, 91, 16 * 1000 + 4, 16 * 2000))
+    assert lib.fbp_volume_create(ctypes.byref(h), bad, 1, 0, 0) == 3         # misaligned
+    bad = (fbp.fbp_item * 1)(fbp.fbp_item(64, 96, 91, None, 16 * 2000))
+    assert lib.fbp_volume_create(ctypes.byref(h), bad, 1, 0, 0) == 1         # NULL buffer
+    assert h.value is None
+    assert lib.fbp_volume_run(None, None) == 1
+    assert lib.fbp_volume_tune(None, None, None, None) == 1
+    assert lib.fbp_volume_info(None, None, None) == 1
+    assert lib.fbp_volume_group(None, 0, None, None, None, None, None, None) == 1
+    assert lib.fbp_volume_destroy(None) == 0
