@@ -18,11 +18,13 @@ dyadic     dyadic patterns, brute-force pattern back projection, the stage-by-st
            Hough transform (float32 or float64) and the quarter sum (Sec. 4.3-4.5, Eq. 16-22)
 fbp        the whole fast method, and the direct Theta(N^3) FBP used as the quality judge
            (Eq. 3-5)
+adjoint    transposes of the filter, the resampling and the back projection (gradients of
+           the fast method with respect to the sinogram)
 
 Readings of the paper that the oracle fixes where the text is silent or garbled are
 listed in each module's docstring.
 """
-from . import ramp, iir, geometry, linogram, dyadic, fbp  # noqa: F401
+from . import ramp, iir, geometry, linogram, dyadic, fbp, adjoint  # noqa: F401
 from .ramp import ramp_h, ramp_h_sinc, causal_part, anticausal_part  # noqa: F401
 from .iir import (iir_causal, iir_anticausal, iir_filter, iir_impulse_response,  # noqa: F401
                   fir_ramp)
@@ -32,3 +34,6 @@ from .dyadic import (dyadic_pattern, pattern_backproject, fht_stages,  # noqa: F
                      combine_quarters)
 from .fbp import (fast_fbp, fast_backproject, fast_fbp_pixels, direct_fbp, direct_fbp_pixels,  # noqa: F401
                   fht_backproject)
+from .adjoint import (quarter_gradients, pattern_backproject_adjoint,  # noqa: F401
+                      fht_stages_adjoint, fht_backproject_adjoint, linogram_adjoint,
+                      fast_fbp_adjoint)

@@ -22,6 +22,12 @@ MISTAKES = [
     ("iir.py", "acc = acc + b[k] * p[..., n - k]", "acc = acc + b[k] * p[..., n - k - 1]"),
     ("ramp.py", "out[n == 0] = 0.25", "out[n == 0] = 0.5"),
     ("fbp.py", "return acc * (np.pi / K)", "return acc * (2 * np.pi / K)"),
+    # adjoints
+    ("adjoint.py", "s0[:, t:] = a0[:, :W - t]", "s0[:, t + 1:] = a0[:, :W - t - 1]"),  # shift
+    ("adjoint.py", "new[0::2, t, :] = a0 + a1", "new[0::2, t, :] = a0"),       # dropped term
+    ("adjoint.py", "np.where(wrap, (M - 1) - m, m).ravel()", "m.ravel()"),     # no mirror
+    ("adjoint.py", "return np.stack([g, g[:, ::-1], g.T, g[::-1, :].T])",
+     "return np.stack([g, g[:, ::-1], g, g[::-1, :].T])"),                    # missing transpose
 ]
 
 
@@ -38,6 +44,6 @@ def test_planted_mistake_is_caught(tmp_path, fname, old, new):
                         "-p", "no:cacheprovider", "tests/test_oracle_ramp.py",
                         "tests/test_oracle_iir.py", "tests/test_oracle_geometry.py",
                         "tests/test_oracle_linogram.py", "tests/test_oracle_dyadic.py",
-                        "tests/test_oracle_fbp.py"],
+                        "tests/test_oracle_fbp.py", "tests/test_oracle_adjoint.py"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, r.stdout[-2000:]
