@@ -136,6 +136,29 @@ fbp_status fbp_reconstruct(fbp_plan_t plan, const float* d_sino, float* d_img, v
 fbp_status fbp_reconstruct_host(fbp_plan_t plan, const float* h_sino, float* h_img, int count,
                                 void* stream);
 
+/* ------------------------------------------------------------------ adjoints
+ * The fast reconstruction is linear in the sinogram, f = H(L(F p)) (F: Eq. 12-13, L:
+ * Eq. 14-15, H: Eq. 16-22); these are its transposes, for gradients with respect to the
+ * sinogram.  The filter is symmetric (causal + anticausal with zero state at both ends), so
+ * fbp_filter_iir is its own adjoint.  Layouts as in the forward calls; `batch` slices.
+ * The first call allocates an adjoint workspace (chunk x (2 linograms + 1 sinogram)). */
+
+/* H^T: image gradient d_img_grad [batch][N][N] -> linogram gradient d_lin_grad
+ * [batch][4][N][2N] (every entry written; zero where no pattern reaches).  Float32, the
+ * stage recursion transposed: bit-reproducible.  Errors as fbp_fht_backproject. */
+fbp_status fbp_fht_backproject_adjoint(fbp_plan_t plan, const float* d_img_grad,
+                                       float* d_lin_grad, void* stream);
+
+/* L^T: linogram gradient [batch][4][N][2N] -> filtered-sinogram gradient [batch][K][M]
+ * (overwritten): each sample's gradient times its four bilinear weights, added with
+ * float atomics (the last bits depend on the order of the additions). */
+fbp_status fbp_resample_st_adjoint(fbp_plan_t plan, const float* d_lin_grad,
+                                   float* d_filt_grad, void* stream);
+
+/* (H L F)^T = F L^T H^T: image gradient [batch][N][N] -> sinogram gradient [batch][K][M]. */
+fbp_status fbp_reconstruct_adjoint(fbp_plan_t plan, const float* d_img_grad,
+                                   float* d_sino_grad, void* stream);
+
 /* ------------------------------------------------------------------ ragged volumes
  * A volume whose slices differ in size (N, K, M), each slice in its own buffers.  No
  * counterpart in the paper (which reconstructs one slice at a time); an execution layer

@@ -67,6 +67,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "fbp_reconstruct": (I, [P, V, V, V]),
         "fbp_reconstruct_host": (I, [P, V, V, I, V]),
         "fbp_direct_reconstruct": (I, [P, V, V, V]),
+        "fbp_fht_backproject_adjoint": (I, [P, V, V, V]),
+        "fbp_resample_st_adjoint": (I, [P, V, V, V]),
+        "fbp_reconstruct_adjoint": (I, [P, V, V, V]),
         "fbp_fht_backproject_static": (I, [I, I, V, V, V]),
         "fbp_plan_info": (I, [P] + [ctypes.POINTER(I)] * 6),
         "fbp_profile_enable": (I, [P, I]),
@@ -265,6 +268,24 @@ def fbp_reconstruct(plan: Plan, sino, img, stream=None) -> None:
     _check("fbp_reconstruct", load_library().fbp_reconstruct(
         plan.handle, _dev_ptr(sino, plan.sino_shape, "sino"),
         _dev_ptr(img, plan.img_shape, "img"), _stream_ptr(stream)))
+
+
+def fbp_fht_backproject_adjoint(plan: Plan, img_grad, lin_grad, stream=None) -> None:
+    _check("fbp_fht_backproject_adjoint", load_library().fbp_fht_backproject_adjoint(
+        plan.handle, _dev_ptr(img_grad, plan.img_shape, "img_grad"),
+        _dev_ptr(lin_grad, plan.lin_shape, "lin_grad"), _stream_ptr(stream)))
+
+
+def fbp_resample_st_adjoint(plan: Plan, lin_grad, filt_grad, stream=None) -> None:
+    _check("fbp_resample_st_adjoint", load_library().fbp_resample_st_adjoint(
+        plan.handle, _dev_ptr(lin_grad, plan.lin_shape, "lin_grad"),
+        _dev_ptr(filt_grad, plan.sino_shape, "filt_grad"), _stream_ptr(stream)))
+
+
+def fbp_reconstruct_adjoint(plan: Plan, img_grad, sino_grad, stream=None) -> None:
+    _check("fbp_reconstruct_adjoint", load_library().fbp_reconstruct_adjoint(
+        plan.handle, _dev_ptr(img_grad, plan.img_shape, "img_grad"),
+        _dev_ptr(sino_grad, plan.sino_shape, "sino_grad"), _stream_ptr(stream)))
 
 
 def fbp_direct_reconstruct(plan: Plan, sino, img, stream=None) -> None:

@@ -572,6 +572,7 @@ fbp_status fbp_plan_destroy(fbp_plan_t p)
     DeviceGuard g(p->device);
     cudaDeviceSynchronize();
     if (p->ws_owned && p->ws) cudaFree(p->ws);
+    if (p->adj_ws) cudaFree(p->adj_ws);
     if (p->d_geom) cudaFree(p->d_geom);
     if (p->d_trig) cudaFree(p->d_trig);
     if (p->d_status) cudaFree(p->d_status);
@@ -749,6 +750,95 @@ fbp_status fbp_reconstruct_host(fbp_plan_t p, const float* h_sino, float* h_img,
     if (e == cudaSuccess) e = cudaEventRecord(p->ev_done, p->st_d2h);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_done, 0);
     return cuda_status(e);
+}
+
+// ------------------------------------------------------------------ adjoints
+namespace {
+
+fbp_status ensure_adjoint_workspace(fbp_plan_s* p)
+{
+    const size_t lin = fbp::lin_floats(p) * sizeof(float);
+    const size_t sino = fbp::sino_floats(p) * sizeof(float);
+    const size_t need = (size_t)p->chunk * (2 * lin + sino);
+    if (p->adj_ws && p->adj_bytes >= need) return FBP_OK;
+    if (p->adj_ws) {
+        cudaDeviceSynchronize();
+        cudaFree(p->adj_ws);
+        p->adj_ws = nullptr;
+        p->adj_bytes = 0;
+    }
+    if (cudaMalloc(&p->adj_ws, need) != cudaSuccess) {
+        cudaGetLastError();
+        p->adj_ws = nullptr;
+        return FBP_ERR_OOM;
+    }
+    p->adj_bytes = need;
+    return FBP_OK;
+}
+
+float* adj_lin(const fbp_plan_s* p, int which)
+{
+    return (float*)p->adj_ws + (size_t)which * p->chunk * fbp::lin_floats(p);
+}
+
+}  // namespace
+
+fbp_status fbp_fht_backproject_adjoint(fbp_plan_t p, const float* d_img_grad, float* d_lin_grad,
+                                       void* stream)
+{
+    if (!p || !d_img_grad || !d_lin_grad) return FBP_ERR_INVALID_ARG;
+    if (!aligned16(d_img_grad) || !aligned16(d_lin_grad)) return FBP_ERR_MISALIGNED;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    fbp_status s = ensure_adjoint_workspace(p);
+    if (s != FBP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int c = 0; c < p->batch; c += p->chunk) {
+        const int cnt = p->batch - c < p->chunk ? p->batch - c : p->chunk;
+        const cudaError_t e = fbp::launch_fht_adjoint(
+            p, d_img_grad + (size_t)c * fbp::img_floats(p),
+            d_lin_grad + (size_t)c * fbp::lin_floats(p), adj_lin(p, 1), cnt, st);
+        if (e != cudaSuccess) return FBP_ERR_CUDA;
+    }
+    return FBP_OK;
+}
+
+fbp_status fbp_resample_st_adjoint(fbp_plan_t p, const float* d_lin_grad, float* d_filt_grad,
+                                   void* stream)
+{
+    if (!p || !d_lin_grad || !d_filt_grad) return FBP_ERR_INVALID_ARG;
+    if (!aligned16(d_lin_grad) || !aligned16(d_filt_grad)) return FBP_ERR_MISALIGNED;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    return cuda_status(fbp::launch_resample_adjoint(p, d_lin_grad, d_filt_grad, p->batch,
+                                                   (cudaStream_t)stream));
+}
+
+fbp_status fbp_reconstruct_adjoint(fbp_plan_t p, const float* d_img_grad, float* d_sino_grad,
+                                   void* stream)
+{
+    if (!p || !d_img_grad || !d_sino_grad) return FBP_ERR_INVALID_ARG;
+    if (!aligned16(d_img_grad) || !aligned16(d_sino_grad)) return FBP_ERR_MISALIGNED;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    fbp_status s = ensure_adjoint_workspace(p);
+    if (s != FBP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    float* lin = adj_lin(p, 0);
+    float* scratch = adj_lin(p, 1);
+    float* pbar = adj_lin(p, 2);
+    for (int c = 0; c < p->batch; c += p->chunk) {
+        const int cnt = p->batch - c < p->chunk ? p->batch - c : p->chunk;
+        cudaError_t e = fbp::launch_fht_adjoint(p, d_img_grad + (size_t)c * fbp::img_floats(p),
+                                                lin, scratch, cnt, st);
+        if (e == cudaSuccess) e = fbp::launch_resample_adjoint(p, lin, pbar, cnt, st);
+        // the filter is its own adjoint (Eq. 12-13: causal + anticausal is symmetric)
+        if (e == cudaSuccess)
+            e = fbp::launch_iir(p, pbar, d_sino_grad + (size_t)c * fbp::sino_floats(p),
+                                cnt * p->K, p->M, st);
+        if (e != cudaSuccess) return FBP_ERR_CUDA;
+    }
+    return FBP_OK;
 }
 
 fbp_status fbp_direct_reconstruct(fbp_plan_t p, const float* d_sino, float* d_img, void* stream)

@@ -71,6 +71,10 @@ struct fbp_plan_s {
     size_t ws_bytes;
     int ws_owned;
     size_t off_filt, off_g, off_stage_sino[2], off_stage_img[2];
+    // adjoint workspace (allocated on first use): per chunk slice two linogram-sized
+    // buffers and one sinogram-sized buffer
+    void* adj_ws;
+    size_t adj_bytes;
     // host-API pipeline
     cudaStream_t st_h2d, st_comp, st_d2h;
     cudaEvent_t ev_start, ev_h2d[2], ev_comp[2], ev_free[2], ev_done;
@@ -102,6 +106,13 @@ cudaError_t launch_pass2(const fbp_plan_s* p, const float* g, float* img, int co
                          bool horizontal, cudaStream_t st, float* const* img_tab = nullptr);
 cudaError_t launch_fir(const fbp_plan_s* p, const float* in, float* out, int rows,
                        cudaStream_t st);
+// Adjoints: image gradient [count][N][N] -> linogram gradient [count][4][N][2N] (scratch:
+// another [count][4][N][2N] buffer), and linogram gradient -> filtered-sinogram gradient
+// [count][K][M] (zeroed, then scattered into).
+cudaError_t launch_fht_adjoint(const fbp_plan_s* p, const float* img_grad, float* lin_grad,
+                               float* scratch, int count, cudaStream_t st);
+cudaError_t launch_resample_adjoint(const fbp_plan_s* p, const float* lin_grad, float* filt_grad,
+                                    int count, cudaStream_t st);
 cudaError_t launch_direct_bp(const fbp_plan_s* p, const float* filt, float* img, int count,
                              cudaStream_t st);
 

@@ -1,0 +1,134 @@
+"""Adjoints on the GPU against the oracle's adjoints, the adjoint identity, and the torch
+autograd wrapper.
+
+Tolerances: the transposed back projection is bit for bit the oracle's float32 transposed
+stage recursion (fixed float32 sums); the transposed resampling and the whole adjoint add
+with float atomics in varying order, so they are compared with the float64 oracle at
+2e-5 of the largest value (float32 weights and positions, like the forward resampling).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import phantoms
+
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-5
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need CUDA"
+    return t
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("N", [2, 4, 8, 16, 64, 128, 256])
+def test_backprojection_adjoint_bit_exact(fbp, torch, N):
+    rng = np.random.default_rng(N)
+    g = rng.normal(size=(2, N, N)).astype(np.float32)
+    K, M = phantoms.geometry_for(N)
+    plan = fbp.fbp_plan(N, K, M, 2)
+    lin = torch.full(plan.lin_shape, float("nan"), device="cuda")
+    fbp.fbp_fht_backproject_adjoint(plan, dev(torch, g), lin)
+    torch.cuda.synchronize()
+    got = lin.cpu().numpy()
+    for b in range(2):
+        want = oracle.fht_backproject_adjoint(g[b])
+        np.testing.assert_array_equal(got[b], want)
+
+
+def test_backprojection_adjoint_integer_inputs_exact(fbp, torch):
+    N = 256
+    rng = np.random.default_rng(9)
+    g = rng.integers(-1024, 1024, size=(1, N, N)).astype(np.float32)
+    K, M = phantoms.geometry_for(N)
+    plan = fbp.fbp_plan(N, K, M, 1)
+    lin = torch.empty(plan.lin_shape, device="cuda")
+    fbp.fbp_fht_backproject_adjoint(plan, dev(torch, g), lin)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(lin.cpu().numpy()[0],
+                                  oracle.fht_backproject_adjoint(g[0].astype(np.float64),
+                                                                 brute=True))
+
+
+@pytest.mark.parametrize("N", [16, 64])
+def test_resampling_adjoint_matches_oracle(fbp, torch, N):
+    rng = np.random.default_rng(N + 1)
+    K, M = phantoms.geometry_for(N)
+    lb = rng.normal(size=(1, 4, N, 2 * N)).astype(np.float32)
+    plan = fbp.fbp_plan(N, K, M, 1)
+    out = torch.full(plan.sino_shape, float("nan"), device="cuda")
+    fbp.fbp_resample_st_adjoint(plan, dev(torch, lb), out)
+    torch.cuda.synchronize()
+    want = oracle.linogram_adjoint(lb[0].astype(np.float64), N, K, M)
+    assert np.abs(out.cpu().numpy()[0] - want).max() <= TOL * np.abs(want).max()
+
+
+def test_reconstruct_adjoint_matches_oracle(fbp, torch, coeff_table):
+    N = 64
+    K, M = phantoms.geometry_for(N)
+    e = next(e for e in coeff_table["entries"] if e["N"] == N and e["order"] == 3)
+    b, a = list(e["b"]), list(e["a"])
+    rng = np.random.default_rng(2)
+    g = rng.normal(size=(2, N, N)).astype(np.float32)
+    plan = fbp.fbp_plan(N, K, M, 2, (b, a))
+    out = torch.empty(plan.sino_shape, device="cuda")
+    fbp.fbp_reconstruct_adjoint(plan, dev(torch, g), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    for s in range(2):
+        want = oracle.fast_fbp_adjoint(g[s].astype(np.float64), N, K, M, b, a)
+        assert np.abs(got[s] - want).max() <= TOL * np.abs(want).max()
+
+
+def test_adjoint_identity_batch_of_512(fbp, torch):
+    # <R x, y> = <x, R^T y> for the GPU operator pair, B = 4 slices of N = 512
+    N, B = 512, 4
+    K, M = phantoms.geometry_for(N)
+    plan = fbp.fbp_plan(N, K, M, B)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn(plan.sino_shape, device="cuda", generator=gen)
+    y = torch.randn(plan.img_shape, device="cuda", generator=gen)
+    rx = torch.empty(plan.img_shape, device="cuda")
+    rty = torch.empty(plan.sino_shape, device="cuda")
+    fbp.fbp_reconstruct(plan, x, rx)
+    fbp.fbp_reconstruct_adjoint(plan, y, rty)
+    torch.cuda.synchronize()
+    lhs = float((rx.double() * y.double()).sum())
+    rhs = float((x.double() * rty.double()).sum())
+    scale = float((rx.double().abs() * y.double().abs()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * scale
+
+
+def test_autograd_gradient_is_the_adjoint(fbp, torch):
+    from paper_2007_06289_gb300 import autograd as fa
+    N, B = 128, 2
+    K, M = phantoms.geometry_for(N)
+    layer = fa.FastFBP(N, K, M, B)
+    sino = phantoms.phantom_stack_torch(N, B, 11, "cuda").requires_grad_(True)
+    w = torch.randn(B, N, N, device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+    img = layer(sino)
+    ref = torch.empty(layer.plan.img_shape, device="cuda")
+    fbp.fbp_reconstruct(layer.plan, sino.detach(), ref)
+    assert torch.equal(img.detach(), ref)
+    (img * w).sum().backward()
+    adj = torch.empty(layer.plan.sino_shape, device="cuda")
+    fbp.fbp_reconstruct_adjoint(layer.plan, w, adj)
+    torch.cuda.synchronize()
+    assert torch.allclose(sino.grad, adj, rtol=0, atol=1e-6 * float(adj.abs().max()))
+    # directional derivatives (the operator is linear, so a finite difference along v is
+    # R v exactly up to rounding): <grad, v> = <w, R v> for 16 random directions
+    gen = torch.Generator(device="cuda").manual_seed(2)
+    for _ in range(16):
+        v = torch.randn(layer.plan.sino_shape, device="cuda", generator=gen)
+        with torch.no_grad():
+            rv = layer(v)
+        lhs = float((sino.grad.double() * v.double()).sum())
+        rhs = float((w.double() * rv.double()).sum())
+        assert abs(lhs - rhs) <= 1e-4 * float((w.double().abs() * rv.double().abs()).sum())
