@@ -55,9 +55,11 @@ def parse_args(argv=None):
     ap.add_argument("--chunk", type=int, default=0, help="slices per launch (0 = library default)")
     ap.add_argument("--sample-pixels", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("stack", "ragged"), default="stack",
+    ap.add_argument("--workload", choices=("stack", "ragged", "adjoint"), default="stack",
                     help="stack: the N = 2048 64-slice stack (default); ragged: a volume of "
-                         "--ragged-slices slices with N drawn uniformly from 256..2048")
+                         "--ragged-slices slices with N drawn uniformly from 256..2048; "
+                         "adjoint: forward and adjoint (gradient) passes on a batch of 32 "
+                         "slices of N = 512")
     ap.add_argument("--ragged-slices", type=int, default=512)
     return ap.parse_args(argv)
 
@@ -547,12 +549,78 @@ def run_ragged(args):
     return line
 
 
+def run_adjoint(args):
+    """Forward reconstruction and its adjoint (the gradient with respect to the sinograms)
+    on a batch of 32 noisy phantom slices of N = 512 (K = 768, M = 725).  One step = one
+    adjoint pass over the batch; the forward pass is timed the same way beside it."""
+    import torch
+
+    import phantoms
+    from paper_2007_06289_gb300 import binding as fbp
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    N, B = 512, 32
+    K, M = phantoms.geometry_for(N)
+    sino = phantoms.phantom_stack_torch(N, B, 2023 + rank * B, dev, noise_i0=I0)
+    plan = fbp.fbp_plan(N, K, M, B)
+    img = torch.empty(plan.img_shape, device=dev)
+    grad = torch.empty(plan.sino_shape, device=dev)
+    w = torch.randn(plan.img_shape, device=dev, generator=torch.Generator(device=dev).manual_seed(3))
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return reduce_max(e0.elapsed_time(e1) / args.steps, world, dev)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms_fwd = timed(lambda: fbp.fbp_reconstruct(plan, sino, img))
+    ms_adj = timed(lambda: fbp.fbp_reconstruct_adjoint(plan, w, grad))
+    clocks = sampler.stop()
+    n = plan.N.bit_length() - 1
+    line = {"metric": "slices/s of the adjoint (sinogram gradient) at N=512, batch 32",
+            "value": round(B * world / (ms_adj / 1e3), 2), "unit": "slices/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms_adj, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: seeded noisy ellipse phantoms (gradient: seeded normal image)",
+            "config": {"workload": "adjoint of the fast FBP, N=512 K=768 M=725, batch 32",
+                       "N": N, "K": K, "M": M, "batch": B, "chunk": plan.chunk,
+                       "l2": "no flush: per-step buffers (sinogram gradients, linogram-"
+                             "sized ping-pong buffers) exceed L2"},
+            "forward": {"value": round(B * world / (ms_fwd / 1e3), 2), "unit": "slices/s",
+                        "ms_per_step": round(ms_fwd, 4)},
+            "clocks": clocks,
+            "gpu_launches": args.steps * -(-B // plan.chunk) * (1 + n + 1 + 1)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "ragged":
         run_ragged(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 
