@@ -434,6 +434,24 @@ __device__ __forceinline__ void resample_row(float* row, const float* ra, int pi
     }
 }
 
+// Asks L2 for the bins a warp's tile row will gather (angle rows k0 and k0+1 over the
+// tile's detector span; nothing for a wrapping row): lanes 0-15 take 32-float lines of row
+// k0, lanes 16-31 of row k0+1.  All addresses stay inside the guarded rows.
+template <int WB>
+__device__ __forceinline__ void prefetch_tile_row(const float* pt, int pitch, int M,
+                                                  const RowGeom& gm, int c0, int lane)
+{
+    if (gm.wrap) return;
+    const long long ma = gm.b_fx + gm.a_fx * (long long)c0;
+    const long long mb = ma + gm.a_fx * (long long)(WB - 1);
+    const int ja = max((int)((ma < mb ? ma : mb) >> kFixBits), -kGuard);
+    const int jb = min((int)((ma < mb ? mb : ma) >> kFixBits) + 1, M + kGuard - 1);
+    if (ja > jb) return;
+    const float* r = pt + (size_t)gm.k0 * pitch + (lane >= 16 ? pitch : 0);
+    const float* a = r + min(ja + 32 * (lane & 15), jb);
+    asm volatile("prefetch.global.L2 [%0];\n" ::"l"(a));
+}
+
 // CTA = (column tile, quarter * blocks + block, slice).  Resamples (or loads) the block's
 // 2^LOGR linogram rows over the tile plus halo, runs LOGR stages, writes G.
 template <int LOGR, bool FROM_LIN>
@@ -474,6 +492,11 @@ pass1_kernel(Pass1Args a)
         const int M = a.M;
         const int pitch = a.pitch;
         constexpr int kS = 4;
+        // start every row of this warp on its way into L2 before gathering any of them
+        for (int j = warp; j < R; j += NWARPS) {
+            const int i = bi * R + j;
+            if (c0 <= N - 1 + i) prefetch_tile_row<WB>(pt, pitch, M, a.geom[q * N + i], c0, lane);
+        }
         for (int j = warp; j < R; j += NWARPS) {
             const int i = bi * R + j;
             const int limit = N - 1 + i;
