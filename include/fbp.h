@@ -149,6 +149,14 @@ fbp_status fbp_reconstruct_host(fbp_plan_t plan, const float* h_sino, float* h_i
 fbp_status fbp_fht_backproject_adjoint(fbp_plan_t plan, const float* d_img_grad,
                                        float* d_lin_grad, void* stream);
 
+/* Eq. 17, the forward direction: the fast Hough (discrete Radon) transform of images
+ * d_img [batch][N][N] in linogram coordinates, d_lin [batch][4][N][2N]: entry [q][i][c] is
+ * the sum of the image's pixels along the dyadic line of quarter q, slope i/(N-1) and
+ * intercept c (the '+' quarters stored flipped as in the back projection).  It is the
+ * transpose of the back projection (the same kernels as fbp_fht_backproject_adjoint), so
+ * <fbp_hough_project(f), L> = <f, fbp_fht_backproject(L)>.  No filtering, no resampling. */
+fbp_status fbp_hough_project(fbp_plan_t plan, const float* d_img, float* d_lin, void* stream);
+
 /* L^T: linogram gradient [batch][4][N][2N] -> filtered-sinogram gradient [batch][K][M]
  * (overwritten): each sample's gradient times its four bilinear weights, added with
  * float atomics (the last bits depend on the order of the additions). */

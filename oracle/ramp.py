@@ -42,3 +42,47 @@ def anticausal_part(n) -> np.ndarray:
     n = np.asarray(n)
     out = np.where(n < 0, ramp_h(n), 0.0)
     return np.where(n == 0, ramp_h(0) / 2.0, out)
+
+
+# Other filters (the end of Sec. 3 notes that the recursive scheme applies to other FBP
+# filters): the ramp |w| apodised by a window on |w| <= 1/2, w in cycles per sample.
+WINDOWS = ("ram-lak", "shepp-logan", "cosine", "hamming", "hann")
+
+
+def window(w, name: str) -> np.ndarray:
+    """Apodisation window W(w): ram-lak 1, shepp-logan sin(pi w)/(pi w), cosine cos(pi w),
+    hamming 0.54 + 0.46 cos(2 pi w), hann 0.5 + 0.5 cos(2 pi w)."""
+    w = np.asarray(w, dtype=np.float64)
+    if name == "ram-lak":
+        return np.ones_like(w)
+    if name == "shepp-logan":
+        return np.sinc(w)
+    if name == "cosine":
+        return np.cos(np.pi * w)
+    if name == "hamming":
+        return 0.54 + 0.46 * np.cos(2 * np.pi * w)
+    if name == "hann":
+        return 0.5 + 0.5 * np.cos(2 * np.pi * w)
+    raise ValueError(name)
+
+
+def windowed_ramp_response(w, name: str) -> np.ndarray:
+    """Ideal frequency response |w| W(w) of the apodised ramp."""
+    return np.abs(np.asarray(w, dtype=np.float64)) * window(w, name)
+
+
+def shepp_logan_h(n) -> np.ndarray:
+    """Impulse response of |w| sin(pi w)/(pi w) on |w| <= 1/2: 2 / (pi^2 (1 - 4 n^2))."""
+    nf = np.asarray(n, dtype=np.float64)
+    return 2.0 / (np.pi ** 2 * (1.0 - 4.0 * nf * nf))
+
+
+def cosine_h(n) -> np.ndarray:
+    """Impulse response of |w| cos(pi w) on |w| <= 1/2: with a = pi (1 +- 2n),
+    h(n) = sum over both a of ((-1)^n / (2a) - 1 / a^2)."""
+    nf = np.asarray(n, dtype=np.float64)
+    sign = np.where(np.asarray(n) % 2 == 0, 1.0, -1.0)
+    out = np.zeros_like(nf)
+    for a in (np.pi * (1.0 + 2.0 * nf), np.pi * (1.0 - 2.0 * nf)):
+        out = out + sign / (2.0 * a) - 1.0 / (a * a)
+    return out

@@ -68,6 +68,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "fbp_reconstruct_host": (I, [P, V, V, I, V]),
         "fbp_direct_reconstruct": (I, [P, V, V, V]),
         "fbp_fht_backproject_adjoint": (I, [P, V, V, V]),
+        "fbp_hough_project": (I, [P, V, V, V]),
         "fbp_resample_st_adjoint": (I, [P, V, V, V]),
         "fbp_reconstruct_adjoint": (I, [P, V, V, V]),
         "fbp_fht_backproject_static": (I, [I, I, V, V, V]),
@@ -274,6 +275,12 @@ def fbp_fht_backproject_adjoint(plan: Plan, img_grad, lin_grad, stream=None) -> 
     _check("fbp_fht_backproject_adjoint", load_library().fbp_fht_backproject_adjoint(
         plan.handle, _dev_ptr(img_grad, plan.img_shape, "img_grad"),
         _dev_ptr(lin_grad, plan.lin_shape, "lin_grad"), _stream_ptr(stream)))
+
+
+def fbp_hough_project(plan: Plan, img, lin, stream=None) -> None:
+    _check("fbp_hough_project", load_library().fbp_hough_project(
+        plan.handle, _dev_ptr(img, plan.img_shape, "img"),
+        _dev_ptr(lin, plan.lin_shape, "lin"), _stream_ptr(stream)))
 
 
 def fbp_resample_st_adjoint(plan: Plan, lin_grad, filt_grad, stream=None) -> None:

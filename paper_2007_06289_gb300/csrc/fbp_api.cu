@@ -803,6 +803,11 @@ fbp_status fbp_fht_backproject_adjoint(fbp_plan_t p, const float* d_img_grad, fl
     return FBP_OK;
 }
 
+fbp_status fbp_hough_project(fbp_plan_t p, const float* d_img, float* d_lin, void* stream)
+{
+    return fbp_fht_backproject_adjoint(p, d_img, d_lin, stream);
+}
+
 fbp_status fbp_resample_st_adjoint(fbp_plan_t p, const float* d_lin_grad, float* d_filt_grad,
                                    void* stream)
 {

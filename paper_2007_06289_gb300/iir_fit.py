@@ -25,7 +25,9 @@ fitting length open.  This module fixes them as follows:
   (variable projection).  Several deterministic starts; the best is kept.
 
 Running this file rewrites the committed table ``iir_coeffs.json`` and the C include
-``csrc/iir_table.inc`` that the library compiles in as its built-in coefficients.
+``csrc/iir_table.inc`` that the library compiles in as its built-in coefficients;
+``--windows`` rewrites ``iir_windows.json``, order-3 fits of the apodised ramps (Shepp-Logan,
+cosine, Hamming, Hann) that callers pass to fbp_plan as explicit coefficients.
 """
 from __future__ import annotations
 
@@ -75,25 +77,50 @@ def _basis(a, Mb, w):
     return np.stack([2.0 * (z ** k / A).real for k in range(Mb)], axis=1)
 
 
-def best_b(a, Mb, w):
-    """Least-squares b with sum(b) = 0 for the given feedback coefficients; returns (b, loss)."""
+# Other FBP filters through the same fit (the end of Sec. 3): the ramp apodised by a window
+# W(w) on |w| <= 1/2; the fit then matches H(w) to |w| W(w), the loss being the mean of
+# ((H(w) - w W(w)) / w)^2 on the same log-spaced grid.
+WINDOWS = ("ram-lak", "shepp-logan", "cosine", "hamming", "hann")
+WINDOW_SIZES = (256, 512, 1024, 2048)       # sizes of the committed windowed-filter table
+
+
+def window(w, name: str = "ram-lak") -> np.ndarray:
+    w = np.asarray(w, dtype=np.float64)
+    if name == "ram-lak":
+        return np.ones_like(w)
+    if name == "shepp-logan":
+        return np.sinc(w)                    # sin(pi w) / (pi w)
+    if name == "cosine":
+        return np.cos(np.pi * w)
+    if name == "hamming":
+        return 0.54 + 0.46 * np.cos(2.0 * np.pi * w)
+    if name == "hann":
+        return 0.5 + 0.5 * np.cos(2.0 * np.pi * w)
+    raise ValueError(f"unknown window {name!r}")
+
+
+def best_b(a, Mb, w, target=None):
+    """Least-squares b with sum(b) = 0 for the given feedback coefficients, matching H(w)/w
+    to `target` (the window; 1 for the plain ramp); returns (b, loss)."""
+    target = np.ones_like(w) if target is None else target
     Phi = _basis(a, Mb, w)
     D = (Phi[:, :-1] - Phi[:, -1:]) / w[:, None]
-    bp, *_ = np.linalg.lstsq(D, np.ones_like(w), rcond=None)
+    bp, *_ = np.linalg.lstsq(D, target, rcond=None)
     b = np.concatenate([bp, [-bp.sum()]])
-    r = Phi @ b / w - 1.0
+    r = Phi @ b / w - target
     return b, float(np.mean(r * r))
 
 
-def fit_coefficients(M: int, order: int, starts: int = 6, seed: int = 7):
+def fit_coefficients(M: int, order: int, starts: int = 6, seed: int = 7, window_name="ram-lak"):
     """Fit Q = Mb = order for a detector of M bins.  Returns (b, a, loss)."""
     from scipy.optimize import minimize
     w = np.geomspace(1.0 / (4 * M), 0.5, 512)
+    target = window(w, window_name)
 
     def loss(x):
         a = reflection_to_poly(KMAX * np.tanh(x))
         excess = np.abs(np.roots(np.concatenate([[1.0], a]))).max() - PMAX
-        return best_b(a, order, w)[1] + (1e3 * excess if excess > 0 else 0.0)
+        return best_b(a, order, w, target)[1] + (1e3 * excess if excess > 0 else 0.0)
 
     rng = np.random.default_rng(seed)
     best = None
@@ -115,7 +142,7 @@ def fit_coefficients(M: int, order: int, starts: int = 6, seed: int = 7):
         if best is None or res.fun < best.fun:
             best = res
     a = reflection_to_poly(KMAX * np.tanh(best.x))
-    b, f = best_b(a, order, w)
+    b, f = best_b(a, order, w, target)
     return b, a, f
 
 
@@ -146,6 +173,39 @@ def coefficients(N: int, order: int = DEFAULT_ORDER, table=None):
     raise KeyError((N, order))
 
 
+def window_coefficients(N: int, window_name: str, order: int = DEFAULT_ORDER, table=None):
+    """(b, a) of the committed windowed-filter table (iir_windows.json); the plain ramp
+    comes from the main table."""
+    if window_name == "ram-lak":
+        return coefficients(N, order)
+    if table is None:
+        with open(os.path.join(_HERE, "iir_windows.json")) as fh:
+            table = json.load(fh)
+    for e in table["entries"]:
+        if e["N"] == N and e["order"] == order and e["window"] == window_name:
+            return np.array(e["b"]), np.array(e["a"])
+    raise KeyError((N, window_name, order))
+
+
+def _fit_window_entry(job):
+    N, window_name = job
+    M = detector_bins(N)
+    b, a, f = fit_coefficients(M, DEFAULT_ORDER, window_name=window_name)
+    return dict(N=N, order=DEFAULT_ORDER, window=window_name, M=M, loss=f,
+                b=list(map(float, b)), a=list(map(float, a)))
+
+
+def fit_windows():
+    """Rewrite iir_windows.json: order-3 fits of every non-trivial window for WINDOW_SIZES."""
+    import multiprocessing as mp
+    jobs = [(N, wn) for N in WINDOW_SIZES for wn in WINDOWS if wn != "ram-lak"]
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+        entries = pool.map(_fit_window_entry, jobs)
+    with open(os.path.join(_HERE, "iir_windows.json"), "w") as fh:
+        json.dump(dict(loss="mean ((H(w) - w W(w)) / w)^2, w log-spaced on [1/(4M), 1/2]",
+                       entries=entries), fh, indent=1)
+
+
 def _fit_entry(job):
     N, order = job
     M = detector_bins(N)
@@ -173,4 +233,7 @@ def main(argv):
 
 
 if __name__ == "__main__":
-    main(sys.argv)
+    if sys.argv[1:2] == ["--windows"]:
+        fit_windows()
+    else:
+        main(sys.argv)

@@ -132,3 +132,29 @@ def test_autograd_gradient_is_the_adjoint(fbp, torch):
         lhs = float((sino.grad.double() * v.double()).sum())
         rhs = float((w.double() * rv.double()).sum())
         assert abs(lhs - rhs) <= 1e-4 * float((w.double().abs() * rv.double().abs()).sum())
+
+
+def test_hough_projector_is_the_transposed_back_projection(fbp, torch):
+    N, B = 128, 2
+    K, M = phantoms.geometry_for(N)
+    plan = fbp.fbp_plan(N, K, M, B)
+    gen = torch.Generator(device="cuda").manual_seed(8)
+    f = torch.randn(plan.img_shape, device="cuda", generator=gen)
+    lin = torch.randn(plan.lin_shape, device="cuda", generator=gen)
+    p1 = torch.empty(plan.lin_shape, device="cuda")
+    p2 = torch.empty(plan.lin_shape, device="cuda")
+    hl = torch.empty(plan.img_shape, device="cuda")
+    fbp.fbp_hough_project(plan, f, p1)
+    fbp.fbp_fht_backproject_adjoint(plan, f, p2)
+    fbp.fbp_fht_backproject(plan, lin.clone(), hl)
+    torch.cuda.synchronize()
+    assert torch.equal(p1, p2)
+    lhs = float((p1.double() * lin.double()).sum())
+    rhs = float((f.double() * hl.double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * float((p1.double().abs() * lin.double().abs()).sum())
+    # a single pixel projects to 1 along each of its dyadic lines: N entries per quarter
+    one = torch.zeros(plan.img_shape, device="cuda")
+    one[0, 37, 90] = 1.0
+    fbp.fbp_hough_project(plan, one, p1)
+    torch.cuda.synchronize()
+    assert float(p1[0].sum()) == 4 * N and int((p1[0] != 0).sum()) == 4 * N

@@ -273,6 +273,23 @@ def test_chunked_batch_and_host_api(fbp, torch, coeff_table):
         fbp.fbp_set_chunk(fbp.fbp_plan(N, K, M, B, co), B + 1)
 
 
+@pytest.mark.parametrize("window", ["shepp-logan", "hann"])
+def test_windowed_filters_match_oracle(fbp, torch, window):
+    # other FBP filters through the recursive fit: the GPU pipeline with those coefficients
+    # against the float64 oracle with the same coefficients
+    from paper_2007_06289_gb300 import iir_fit
+    N = 256
+    K, M = phantoms.geometry_for(N)
+    b, a = iir_fit.window_coefficients(N, window)
+    s = phantoms.phantom_stack(N, 1, 77, noise_i0=1e5)
+    plan = fbp.fbp_plan(N, K, M, 1, (list(b), list(a)))
+    img = torch.empty(plan.img_shape, device="cuda")
+    fbp.fbp_reconstruct(plan, dev(torch, s), img)
+    torch.cuda.synchronize()
+    want = oracle.fast_fbp(s[0].astype(np.float64), N, b, a)
+    assert np.abs(host(img)[0] - want).max() <= TOL_PIPE * (want.max() - want.min())
+
+
 def test_linearity(fbp, torch, coeff_table):
     N = 128
     K, M = phantoms.geometry_for(N)
