@@ -28,6 +28,11 @@ MISTAKES = [
     ("adjoint.py", "np.where(wrap, (M - 1) - m, m).ravel()", "m.ravel()"),     # no mirror
     ("adjoint.py", "return np.stack([g, g[:, ::-1], g.T, g[::-1, :].T])",
      "return np.stack([g, g[:, ::-1], g, g[::-1, :].T])"),                    # missing transpose
+    # CNN corrector
+    ("cnn.py", "xp[:, dy:dy + H, dx:dx + W])\n    return out",
+     "xp[:, 2 - dy:2 - dy + H, 2 - dx:2 - dx + W])\n    return out"),         # convolution, not correlation
+    ("cnn.py", "gh = gin * (hin > 0.0)", "gh = gin"),                          # ReLU mask dropped
+    ("cnn.py", "return x + h[0], cache", "return h[0], cache"),                 # no skip connection
 ]
 
 
@@ -44,6 +49,7 @@ def test_planted_mistake_is_caught(tmp_path, fname, old, new):
                         "-p", "no:cacheprovider", "tests/test_oracle_ramp.py",
                         "tests/test_oracle_iir.py", "tests/test_oracle_geometry.py",
                         "tests/test_oracle_linogram.py", "tests/test_oracle_dyadic.py",
-                        "tests/test_oracle_fbp.py", "tests/test_oracle_adjoint.py"],
+                        "tests/test_oracle_fbp.py", "tests/test_oracle_adjoint.py",
+                        "tests/test_oracle_cnn.py"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, r.stdout[-2000:]
