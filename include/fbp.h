@@ -167,6 +167,36 @@ fbp_status fbp_resample_st_adjoint(fbp_plan_t plan, const float* d_lin_grad,
 fbp_status fbp_reconstruct_adjoint(fbp_plan_t plan, const float* d_img_grad,
                                    float* d_sino_grad, void* stream);
 
+/* ------------------------------------------------------------------ learned corrector
+ * A residual CNN applied after the fast reconstruction, y = x + net(x): six 3x3
+ * convolutions (1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1 channels, zero padding, ReLU between),
+ * trained to map fast images towards direct-FBP images.  No counterpart in the paper: a
+ * learned extension.  Parameters: one fp32 device array of fbp_cnn_param_count() floats,
+ * layer after layer, each layer's weights [co][ci][3][3] then its biases [co].  The four
+ * 32 -> 32 layers run as bf16 tensor-core implicit GEMMs with fp32 accumulation (hidden
+ * activations are stored as bf16); the first and last layers and the weight gradients in
+ * fp32.  Images: [batch][N][N] fp32, N a power of two in 16..4096.  The caller provides the
+ * workspace (16-byte aligned). */
+size_t fbp_cnn_param_count(void);
+
+/* Workspace bytes for `batch` images of N x N; train != 0 keeps the activations for
+ * fbp_cnn_backward.  0 for unsupported sizes. */
+size_t fbp_cnn_workspace_bytes(int N, int batch, int train);
+
+/* d_y = d_x + net(d_x).  With train != 0 the activations stay in the workspace for a
+ * following fbp_cnn_backward on the same images.  Errors: FBP_ERR_UNSUPPORTED (N),
+ * FBP_ERR_INVALID_ARG (NULL, workspace too small), FBP_ERR_MISALIGNED, FBP_ERR_CUDA. */
+fbp_status fbp_cnn_forward(const float* d_params, const float* d_x, float* d_y, void* d_ws,
+                           size_t ws_bytes, int N, int batch, int train, void* stream);
+
+/* Gradient of a loss with respect to the parameters, given its gradient d_gy with respect
+ * to the output of the preceding fbp_cnn_forward(train = 1) call on the same workspace and
+ * images: d_gparams [fbp_cnn_param_count()] is overwritten (float atomics: the last bits
+ * depend on the order of the additions). */
+fbp_status fbp_cnn_backward(const float* d_params, const float* d_x, const float* d_gy,
+                            float* d_gparams, void* d_ws, size_t ws_bytes, int N, int batch,
+                            void* stream);
+
 /* ------------------------------------------------------------------ ragged volumes
  * A volume whose slices differ in size (N, K, M), each slice in its own buffers.  No
  * counterpart in the paper (which reconstructs one slice at a time); an execution layer

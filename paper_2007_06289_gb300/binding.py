@@ -78,6 +78,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "fbp_profile_read": (I, [P, I, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_longlong)]),
         "fbp_status_str": (ctypes.c_char_p, [I]),
+        "fbp_cnn_param_count": (S, []),
+        "fbp_cnn_workspace_bytes": (S, [I, I, I]),
+        "fbp_cnn_forward": (I, [V, V, V, V, S, I, I, I, V]),
+        "fbp_cnn_backward": (I, [V, V, V, V, V, S, I, I, V]),
         "fbp_volume_create": (I, [ctypes.POINTER(P), ctypes.POINTER(fbp_item), I, I, I]),
         "fbp_volume_run": (I, [P, V]),
         "fbp_volume_tune": (I, [P, V, ctypes.POINTER(I), ctypes.POINTER(I)]),
@@ -427,3 +431,37 @@ def fbp_volume_group(volume: Volume, i: int) -> dict:
 
 def fbp_volume_destroy(volume: Volume) -> None:
     volume.close()
+
+
+# ----------------------------------------------------------------------------- learned corrector
+def fbp_cnn_param_count() -> int:
+    return int(load_library().fbp_cnn_param_count())
+
+
+def fbp_cnn_workspace_bytes(N: int, batch: int, train: bool) -> int:
+    return int(load_library().fbp_cnn_workspace_bytes(int(N), int(batch), int(bool(train))))
+
+
+def _ws_ptr(ws):
+    import torch
+    if not isinstance(ws, torch.Tensor) or not ws.is_cuda or not ws.is_contiguous():
+        raise ValueError("ws: expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(ws.data_ptr()), ws.numel() * ws.element_size()
+
+
+def fbp_cnn_forward(params, x, y, ws, train: bool = False, stream=None) -> None:
+    """y = x + net(x) for x [batch][N][N] (float32 CUDA); ws from fbp_cnn_workspace_bytes."""
+    B, N = x.shape[0], x.shape[-1]
+    p, nb = _ws_ptr(ws)
+    _check("fbp_cnn_forward", load_library().fbp_cnn_forward(
+        _dev_ptr(params, (fbp_cnn_param_count(),), "params"), _dev_ptr(x, (B, N, N), "x"),
+        _dev_ptr(y, (B, N, N), "y"), p, nb, N, B, int(bool(train)), _stream_ptr(stream)))
+
+
+def fbp_cnn_backward(params, x, gy, gparams, ws, stream=None) -> None:
+    B, N = x.shape[0], x.shape[-1]
+    p, nb = _ws_ptr(ws)
+    _check("fbp_cnn_backward", load_library().fbp_cnn_backward(
+        _dev_ptr(params, (fbp_cnn_param_count(),), "params"), _dev_ptr(x, (B, N, N), "x"),
+        _dev_ptr(gy, (B, N, N), "gy"), _dev_ptr(gparams, (fbp_cnn_param_count(),), "gparams"),
+        p, nb, N, B, _stream_ptr(stream)))
