@@ -55,11 +55,13 @@ def parse_args(argv=None):
     ap.add_argument("--chunk", type=int, default=0, help="slices per launch (0 = library default)")
     ap.add_argument("--sample-pixels", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("stack", "ragged", "adjoint"), default="stack",
+    ap.add_argument("--workload", choices=("stack", "ragged", "adjoint", "corrector"),
+                    default="stack",
                     help="stack: the N = 2048 64-slice stack (default); ragged: a volume of "
                          "--ragged-slices slices with N drawn uniformly from 256..2048; "
                          "adjoint: forward and adjoint (gradient) passes on a batch of 32 "
-                         "slices of N = 512")
+                         "slices of N = 512; corrector: the learned CNN corrector, inference "
+                         "on 8 slices of N = 2048 and a training step on 4 of N = 512")
     ap.add_argument("--ragged-slices", type=int, default=512)
     return ap.parse_args(argv)
 
@@ -619,6 +621,91 @@ def run_adjoint(args):
     return line
 
 
+def run_corrector(args):
+    """The learned corrector: inference over 8 fast-FBP images of N = 2048 (one step = one
+    fbp_cnn_forward over the batch) and, beside it, one training step (forward with saved
+    activations + backward) on 4 images of N = 512.  The dominant kernel is the bf16
+    tensor-core 3x3 convolution (4 of the 6 layers): 2 x 32 x 288 flops per pixel per layer."""
+    import numpy as np
+    import torch
+
+    import phantoms
+    from paper_2007_06289_gb300 import binding as fbp
+    from paper_2007_06289_gb300 import corrector
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    N, B = 2048, min(8, args.slices)
+    K, M = phantoms.geometry_for(N)
+    sino = phantoms.phantom_stack_torch(N, B, 2025 + rank * B, dev, noise_i0=I0)
+    x = torch.empty(B, N, N, device=dev)
+    fbp.fbp_reconstruct(fbp.fbp_plan(N, K, M, B), sino, x)
+    params = torch.tensor(corrector.init_params(0), device=dev)
+    y = torch.empty_like(x)
+    ws = torch.empty(fbp.fbp_cnn_workspace_bytes(N, B, False), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return reduce_max(e0.elapsed_time(e1) / steps, world, dev)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms_inf = timed(lambda: fbp.fbp_cnn_forward(params, x, y, ws), args.steps)
+    Nt, Bt = 512, min(4, B)
+    xt = x[:, :Nt, :Nt].contiguous()[:Bt].contiguous()
+    tt = (xt * 1.01).contiguous()
+    pt = params.clone().requires_grad_(True)
+
+    def train_step():
+        yt = corrector.correct(pt, xt)
+        loss = torch.mean((yt - tt) ** 2)
+        loss.backward()
+        pt.grad = None
+
+    ms_train = timed(train_step, max(3, args.steps // 3))
+    clocks = sampler.stop()
+    flops_px = 2 * (32 * 9) + 4 * 2 * (32 * 32 * 9) + 2 * (32 * 9)
+    tflops = B * N * N * flops_px / (ms_inf / 1e3) / 1e12
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
+    line = {"metric": "slices/s of the learned corrector (inference) at N=2048",
+            "value": round(B * world / (ms_inf / 1e3), 2), "unit": "slices/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms_inf, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic: fast reconstructions of seeded noisy ellipse phantoms; "
+                    "He-normal weights",
+            "config": {"workload": f"CNN corrector, 6 layers 3x3, 32 channels, N=2048 batch {B}",
+                       "l2": "no flush: bf16 activations of 8 images (2.1 GB) exceed L2"},
+            "roofline": {"bound": "tensor", "kernel": "whole corrector (4 tensor-core layers + "
+                                                      "2 fp32 layers)",
+                         "achieved": round(tflops, 1), "peak": peak, "unit": "TFLOP/s",
+                         "frac": round(tflops / peak, 4), "traffic": None,
+                         "peak_source": "measured bf16 (cuBLAS burst)"},
+            "training_step_ms_N512_batch4": round(ms_train, 3),
+            "clocks": clocks,
+            "gpu_launches": args.steps * 10}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -627,6 +714,8 @@ def main(argv=None):
         run_ragged(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
+    elif args.workload == "corrector":
+        run_corrector(args)
     else:
         run_ours(args)
 
