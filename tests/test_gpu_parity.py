@@ -4,7 +4,7 @@ Tolerances (derivations in the design notes):
 * recursive filter: max |gpu - oracle| <= 1e-5 * max |oracle| (float32 parallel form;
   measured float32 error ~2e-6 of the peak);
 * resampling: max |gpu - oracle| <= 2e-6 * max|p~| * max(w) (float32 bilinear weights of
-  float32 samples, positions carried in double-float);
+  float32 samples, positions carried in 32.32 fixed point);
 * Hough back projection: bit for bit against the float32 stage recursion, and exactly equal
   to float64 brute-force pattern sums on integer-valued inputs;
 * whole pipeline: max |gpu - oracle| <= 1e-5 * (max - min) of the image (float64 oracle);
