@@ -234,6 +234,26 @@ def test_pipeline_matches_fp64_oracle_at_full_size(fbp, torch, coeff_table):
         assert np.abs(got[ys, xs] - want).max() <= TOL_PIPE * (got.max() - got.min())
 
 
+def test_pipeline_matches_fp64_oracle_at_largest_size(fbp, torch, coeff_table):
+    # N = 4096 (K = 6144, M = 5793), the largest supported size: two slices, sampled pixels
+    N, B = 4096, 2
+    K, M = phantoms.geometry_for(N)
+    sino = phantoms.phantom_stack_torch(N, B, 4096, "cuda", noise_i0=1e5)
+    co = coeffs(coeff_table, N, 3)
+    plan = fbp.fbp_plan(N, K, M, B, co)
+    img = torch.empty(plan.img_shape, device="cuda")
+    fbp.fbp_reconstruct(plan, sino, img)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    s = host(sino[1]).astype(np.float64)
+    got = host(img[1])
+    ys, xs = rng.integers(0, N, 12), rng.integers(0, N, 12)
+    ys[:2] = [0, N - 1]
+    xs[:2] = [N - 1, 0]
+    want = oracle.fast_fbp_pixels(s, N, *co, ys, xs)
+    assert np.abs(got[ys, xs] - want).max() <= TOL_PIPE * (got.max() - got.min())
+
+
 def test_chunked_batch_and_host_api(fbp, torch, coeff_table):
     # Chunks of 4 slices: a batch of 5 ends with a ragged chunk (and the host path, which
     # stages 2 slices per copy, with a ragged stage).
