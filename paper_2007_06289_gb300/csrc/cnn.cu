@@ -5,7 +5,8 @@
 // Data layout: hidden activations are bf16 [batch][N][N][32], channel fastest (one pixel's
 // 32 channels are 64 contiguous bytes).  The four 32 -> 32 layers run on the tensor cores
 // as implicit GEMMs (pixels x output channels x (taps x input channels), bf16 operands,
-// fp32 accumulation, mma.sync m16n8k16 fed by ldmatrix from padded shared tiles); the
+// fp32 accumulation, mma.sync m16n8k16 fed by ldmatrix from padded shared tiles, persistent
+// CTAs with double-buffered asynchronous tile loads); the
 // 1 -> 32 and 32 -> 1 layers, the last layer's gradient and the weight gradients run on the
 // CUDA cores in fp32.  The data gradient of a 32 -> 32 layer is the same tensor-core kernel
 // with the layer's weights transposed (input and output channels swapped, taps mirrored)
@@ -23,7 +24,7 @@ namespace {
 constexpr int kC = 32;            // hidden channels
 constexpr int kTaps = 9;
 constexpr int kK = kC * kTaps;    // GEMM depth of a 32 -> 32 layer
-constexpr int kTileY = 8, kTileX = 16;           // output pixels per CTA of the tensor kernel
+constexpr int kTileY = 8, kTileX = 16;           // pixels per tile of the weight-gradient kernel
 constexpr int kHaloY = kTileY + 2, kHaloX = kTileX + 2;
 constexpr int kPixStride = 40;    // bf16 per shared pixel (80 bytes: conflict-free ldmatrix)
 constexpr int kWStride = kK + 8;  // bf16 per shared weight row (592 bytes: conflict-free)
@@ -69,82 +70,135 @@ __global__ void cnn_prep_weights_kernel(const float* __restrict__ w, bf16* __res
 
 // ---------------------------------------------------------------- 32 -> 32 on tensor cores
 // out[p][o] = bias[o] + sum_{tap, c} W[o][tap][c] in[p + off(tap)][c], optional ReLU, optional
-// mask (out *= mask[p][o] > 0).  CTA = 8 x 16 output pixels, warp = one row of 16 pixels.
+// mask (out *= mask[p][o] > 0).  Persistent CTAs: the layer's weights are staged once per
+// CTA; the CTA then walks 16 x 16-pixel output tiles, the next tile's input (with its
+// one-pixel halo) arriving by asynchronous copies into the second of two shared buffers
+// while the tensor cores work on the current one.  Warp w computes output rows 2w and 2w+1
+// of a tile (two 16-pixel M tiles sharing every weight fragment).
+constexpr int kT2 = 16;                           // output tile: 16 x 16 pixels
+constexpr int kH2 = kT2 + 2;                      // with the halo
+constexpr int kActElems = kH2 * kH2 * kPixStride; // bf16 per activation buffer
+constexpr size_t kConvSmem = (size_t)(kC * kWStride + 2 * kActElems) * sizeof(bf16);
+
+__device__ __forceinline__ void cp_async16z(void* dst, const void* src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)),
+                 "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+// the input tile of output tile t (image, ty, tx) with its halo, zero outside the image
+__device__ __forceinline__ void conv_prefetch(bf16* act, const bf16* in, long long t, int N,
+                                              int tiles_x, int tiles_per_img, int tid)
+{
+    const int im = (int)(t / tiles_per_img);
+    const int rem = (int)(t - (long long)im * tiles_per_img);
+    const int y0 = (rem / tiles_x) * kT2, x0 = (rem % tiles_x) * kT2;
+    const size_t img = (size_t)im * N * N;
+    for (int e = tid; e < kH2 * kH2 * 4; e += 256) {
+        const int pix = e >> 2, part = e & 3;
+        const int ty = pix / kH2, tx = pix - ty * kH2;
+        const int gy = y0 - 1 + ty, gx = x0 - 1 + tx;
+        const bool ok = gy >= 0 && gy < N && gx >= 0 && gx < N;
+        const bf16* src = ok ? in + (img + (size_t)gy * N + gx) * kC + part * 8 : in;
+        cp_async16z(act + pix * kPixStride + part * 8, src, ok);
+    }
+}
+
 template <bool BIAS, bool RELU, bool MASK>
 __global__ void __launch_bounds__(256)
 cnn_conv32_kernel(const bf16* __restrict__ in, const bf16* __restrict__ wt,
                   const float* __restrict__ bias, const bf16* __restrict__ mask,
-                  bf16* __restrict__ out, int N)
+                  bf16* __restrict__ out, int N, int images)
 {
-    __shared__ __align__(16) bf16 act[kHaloY * kHaloX * kPixStride];
-    __shared__ __align__(16) bf16 wsm[kC * kWStride];
-    const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
-    const size_t img = (size_t)blockIdx.z * N * N;
+    extern __shared__ __align__(16) unsigned char conv_smem[];
+    bf16* wsm = reinterpret_cast<bf16*>(conv_smem);
+    bf16* act0 = wsm + kC * kWStride;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = N / kT2, tiles_per_img = tiles_x * (N / kT2);
+    const long long total = (long long)tiles_per_img * images;
 
-    // input tile with a one-pixel halo (zero outside the image), 16-byte chunks
-    for (int e = tid; e < kHaloY * kHaloX * 4; e += 256) {
-        const int pix = e >> 2, part = e & 3;
-        const int ty = pix / kHaloX, tx = pix - ty * kHaloX;
-        const int gy = y0 - 1 + ty, gx = x0 - 1 + tx;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (gy >= 0 && gy < N && gx >= 0 && gx < N)
-            v = *reinterpret_cast<const uint4*>(in + (img + (size_t)gy * N + gx) * kC + part * 8);
-        *reinterpret_cast<uint4*>(act + pix * kPixStride + part * 8) = v;
-    }
     for (int e = tid; e < kC * (kK / 8); e += 256) {
         const int row = e / (kK / 8), part = e - row * (kK / 8);
         *reinterpret_cast<uint4*>(wsm + row * kWStride + part * 8) =
             *reinterpret_cast<const uint4*>(wt + (size_t)row * kK + part * 8);
     }
-    __syncthreads();
-
-    float acc[4][4];
-#pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) acc[nt][k] = 0.0f;
+    long long t = blockIdx.x;
+    if (t < total) conv_prefetch(act0, in, t, N, tiles_x, tiles_per_img, tid);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
 
     const int j = lane >> 3, r = lane & 7;
-#pragma unroll 1
-    for (int tap = 0; tap < kTaps; ++tap) {
-        const int dy = tap / 3, dx = tap - 3 * (tap / 3);
-#pragma unroll
-        for (int cb = 0; cb < 2; ++cb) {
-            unsigned a[4];
-            const int xx = r + 8 * (j & 1);
-            ldmatrix_x4(a, act + ((warp + dy) * kHaloX + xx + dx) * kPixStride + cb * 16 + 8 * (j >> 1));
-            const int kb = tap * kC + cb * 16;
-#pragma unroll
-            for (int pr = 0; pr < 2; ++pr) {
-                unsigned b[4];
-                ldmatrix_x4(b, wsm + ((2 * pr + (j >> 1)) * 8 + r) * kWStride + kb + 8 * (j & 1));
-                mma_bf16(acc[2 * pr], a, b[0], b[1]);
-                mma_bf16(acc[2 * pr + 1], a, b[2], b[3]);
-            }
-        }
-    }
+    const int g = lane >> 2, q4 = lane & 3;
+    for (int it = 0; t < total; ++it, t += gridDim.x) {
+        bf16* act = act0 + (it & 1) * kActElems;
+        const long long tn = t + gridDim.x;
+        if (tn < total)
+            conv_prefetch(act0 + ((it + 1) & 1) * kActElems, in, tn, N, tiles_x, tiles_per_img, tid);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        __syncthreads();
 
-    const int g = lane >> 2, t = lane & 3;
-    const int py = y0 + warp;
+        float acc[2][4][4];
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        const int ch = nt * 8 + 2 * t;
+        for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int px = x0 + g + 8 * half;
-            const size_t p = (img + (size_t)py * N + px) * kC + ch;
-            float v0 = acc[nt][2 * half], v1 = acc[nt][2 * half + 1];
-            if (BIAS) { v0 += bias[ch]; v1 += bias[ch + 1]; }
-            if (RELU) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
-            if (MASK) {
-                const float2 m = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(mask + p));
-                v0 = m.x > 0.0f ? v0 : 0.0f;
-                v1 = m.y > 0.0f ? v1 : 0.0f;
+            for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[mt][nt][k] = 0.0f;
+#pragma unroll 1
+        for (int tap = 0; tap < kTaps; ++tap) {
+            const int dy = tap / 3, dx = tap - 3 * (tap / 3);
+#pragma unroll
+            for (int cb = 0; cb < 2; ++cb) {
+                unsigned a[2][4];
+                const int xx = r + 8 * (j & 1);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+                    ldmatrix_x4(a[mt], act + ((2 * warp + mt + dy) * kH2 + xx + dx) * kPixStride +
+                                           cb * 16 + 8 * (j >> 1));
+                const int kb = tap * kC + cb * 16;
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+                    unsigned bb[4];
+                    ldmatrix_x4(bb, wsm + ((2 * pr + (j >> 1)) * 8 + r) * kWStride + kb + 8 * (j & 1));
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        mma_bf16(acc[mt][2 * pr], a[mt], bb[0], bb[1]);
+                        mma_bf16(acc[mt][2 * pr + 1], a[mt], bb[2], bb[3]);
+                    }
+                }
             }
-            *reinterpret_cast<__nv_bfloat162*>(out + p) = __floats2bfloat162_rn(v0, v1);
         }
+
+        const int im = (int)(t / tiles_per_img);
+        const int rem = (int)(t - (long long)im * tiles_per_img);
+        const int y0 = (rem / tiles_x) * kT2, x0 = (rem % tiles_x) * kT2;
+        const size_t img = (size_t)im * N * N;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            const int py = y0 + 2 * warp + mt;
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) {
+                const int ch = nt * 8 + 2 * q4;
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const int px = x0 + g + 8 * half;
+                    const size_t p = (img + (size_t)py * N + px) * kC + ch;
+                    float v0 = acc[mt][nt][2 * half], v1 = acc[mt][nt][2 * half + 1];
+                    if (BIAS) { v0 += bias[ch]; v1 += bias[ch + 1]; }
+                    if (RELU) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
+                    if (MASK) {
+                        const float2 m = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(mask + p));
+                        v0 = m.x > 0.0f ? v0 : 0.0f;
+                        v1 = m.y > 0.0f ? v1 : 0.0f;
+                    }
+                    *reinterpret_cast<__nv_bfloat162*>(out + p) = __floats2bfloat162_rn(v0, v1);
+                }
+            }
+        }
+        __syncthreads();                          // this buffer is refilled two tiles on
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 // ---------------------------------------------------------------- 1 -> 32 and 32 -> 1
@@ -390,6 +444,33 @@ Ws carve(void* ws, int N, int batch)
     return w;
 }
 
+template <bool BIAS, bool RELU, bool MASK>
+cudaError_t launch_conv32(const bf16* in, const bf16* wt, const float* bias, const bf16* mask,
+                          bf16* out, int N, int batch, int sms, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e = cudaFuncSetAttribute(cnn_conv32_kernel<BIAS, RELU, MASK>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)kConvSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long long tiles = (long long)(N / kT2) * (N / kT2) * batch;
+    const int grid = (int)(tiles < 3LL * sms ? tiles : 3LL * sms);
+    cnn_conv32_kernel<BIAS, RELU, MASK><<<grid, 256, kConvSmem, st>>>(in, wt, bias, mask, out, N, batch);
+    return cudaGetLastError();
+}
+
+int device_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return sms;
+}
+
 cudaError_t forward(const float* params, const float* x, float* y, void* ws, int N, int batch,
                     int save, cudaStream_t st)
 {
@@ -401,11 +482,13 @@ cudaError_t forward(const float* params, const float* x, float* y, void* ws, int
     // h1 .. h5 in act[0..4] when saving for the backward pass, else ping-pong in act[0..1]
     auto hbuf = [&](int k) { return save ? w.act[k] : w.act[k & 1]; };
     cnn_first_kernel<<<pg, 256, 0, st>>>(x, params, params + kC * kTaps, hbuf(0), N);
-    const dim3 tg(N / kTileX, N / kTileY, batch);
+    const int sms = device_sms();
+    if (sms <= 0) return cudaErrorInvalidDevice;
     for (int k = 1; k <= 4; ++k) {
         const float* b = params + param_offset(k) + (size_t)kC * kC * kTaps;
-        cnn_conv32_kernel<true, true, false><<<tg, 256, 0, st>>>(hbuf(k - 1), w.wf[k - 1], b,
-                                                                  nullptr, hbuf(k), N);
+        const cudaError_t e = launch_conv32<true, true, false>(hbuf(k - 1), w.wf[k - 1], b,
+                                                               nullptr, hbuf(k), N, batch, sms, st);
+        if (e != cudaSuccess) return e;
     }
     cnn_last_kernel<<<pg, 256, 0, st>>>(x, hbuf(4), params + param_offset(5), y, N);
     return cudaGetLastError();
@@ -418,7 +501,6 @@ cudaError_t backward(const float* params, const float* x, const float* gy, float
     cudaError_t e = cudaMemsetAsync(gparams, 0, param_count() * sizeof(float), st);
     if (e != cudaSuccess) return e;
     const dim3 pg((N * N + 255) / 256, batch);
-    const dim3 tg(N / kTileX, N / kTileY, batch);
     const int wgrid = 2 * sms;
     bf16* g[2] = {w.act[5], w.act[6]};
     // layer 6 (32 -> 1): weights from h5 and gy; gradient into z5
@@ -431,8 +513,9 @@ cudaError_t backward(const float* params, const float* x, const float* gy, float
         gw = gparams + param_offset(k);
         cnn_wgrad_kernel<kC, kC><<<wgrid, 256, 0, st>>>(g[cur], w.act[k - 1], gw,
                                                         gw + kC * kC * kTaps, N, batch);
-        cnn_conv32_kernel<false, false, true><<<tg, 256, 0, st>>>(g[cur], w.wb[k - 1], nullptr,
-                                                                   w.act[k - 1], g[cur ^ 1], N);
+        e = launch_conv32<false, false, true>(g[cur], w.wb[k - 1], nullptr, w.act[k - 1],
+                                              g[cur ^ 1], N, batch, sms, st);
+        if (e != cudaSuccess) return e;
         cur ^= 1;
     }
     // layer 1 (1 -> 32): weights from x and g_z1
