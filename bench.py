@@ -613,7 +613,9 @@ def run_adjoint(args):
             "forward": {"value": round(B * world / (ms_fwd / 1e3), 2), "unit": "slices/s",
                         "ms_per_step": round(ms_fwd, 4)},
             "clocks": clocks,
-            "gpu_launches": args.steps * -(-B // plan.chunk) * (1 + n + 1 + 1)}
+            # per chunk: ceil(n / 5) fused transposed-stage launches, the resampling
+            # adjoint, the filter
+            "gpu_launches": args.steps * -(-B // plan.chunk) * (-(-n // 5) + 1 + 1)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -9,9 +9,10 @@
 //     A_{k-1}[2b][t][u]   = A_k[b][2t][u] + A_k[b][2t+1][u]
 //     A_{k-1}[2b+1][t][v] = A_k[b][2t][v - t] + A_k[b][2t+1][v - t - 1]
 // (columns below 0 read as zero), starting from the quarter gradients of Eq. 22's index maps
-// and ending with L-bar[i][c] = A_0[i][0][c].  One launch per stage over all slices and
-// quarters, ping-ponging between two [count][4][N][2N] buffers; every output element is
-// one fixed float32 sum, so the result is reproducible bit for bit.
+// and ending with L-bar[i][c] = A_0[i][0][c].  Up to five stages run per launch in shared
+// memory (below), over all slices and quarters, ping-ponging between two [count][4][N][2N]
+// buffers; every output element is one fixed float32 sum, so the result is reproducible bit
+// for bit.
 //
 // Resampling, transposed.  Each linogram sample is w0 * lerp(row k0) + w1 * lerp(row k1)
 // (Eq. 14-15 with the float32 weights the forward kernels use); its transpose adds the
@@ -23,54 +24,164 @@ namespace fbp {
 namespace {
 
 constexpr int kAdjThreads = 256;
+constexpr int kAfMaxStages = 5;
 
-// Quarter gradients (transpose of Eq. 22's sum): g[N][N] -> A_n[4][N][W], zero for u >= N.
-//   v-: g[tau][u]   v+: g[tau][N-1-u]   h-: g[u][tau]   h+: g[N-1-u][tau]
+// ---------------------------------------------------------------- fused transposed stages
+// One launch runs S consecutive transposed stages, level k -> level k - S, in shared memory.
+//
+// Groups.  Output strip b 2^S + C (C in [0, 2^S)), slope t at level k - S depends only on the
+// 2^S consecutive level-k rows b 2^k + 2^S t + j of strip b: unrolling the stage formula S
+// times,
+//     A_{k-S}[b 2^S + C][t][v] = sum_j A_k[b][2^S t + j][v - C t - s(C, j)],
+// the shift splitting into C t (C read with its first stage's bit highest) and a small part
+// s(C, j) in [0, 2^S - 1] that is exactly the shift of the same S stages run on the 2^S rows
+// alone (slope t = 0).  A CTA therefore loads its group's 2^S rows over a tile of columns
+// x plus a halo of 2^S - 1, runs the S stages on them in shared memory with the small
+// slopes, and writes output row C at column x + C t (a skewed tile).  Each output is the same
+// float32 sum in the same order as one launch per stage: the result is reproducible bit for
+// bit, and equal to the stage-by-stage recursion.
+//
+// Written ranges.  Level-k row (b, tau) can be non-zero only on columns
+// [b tau, b tau + N + 2^(n-k) - 1) (its inputs are image columns [0, N) moved right by
+// b tau plus at most 2^(n-k) - 1).  Each launch computes and writes exactly that range of
+// its output rows (clipped to the row width W = 2N), and reads its input rows as zero outside
+// theirs, so the level arrays between launches are never cleared; the last launch (level 0,
+// the linogram gradient) writes every column.
+template <int S> constexpr int af_halo() { return ((1 << S) - 1 + 3) & ~3; }
+constexpr int kAfCols = kAdjThreads;            // shared-memory columns: one per thread
+template <int S> constexpr int af_tile() { return kAfCols - af_halo<S>(); }
+constexpr int kAfPitch = kAfCols + 1;           // odd: conflict-free column-wise writes
+template <int S> constexpr size_t af_smem() { return 2 * (size_t)(1 << S) * kAfPitch * sizeof(float); }
+
+template <int S, bool FROM_IMAGE>
 __global__ void __launch_bounds__(kAdjThreads)
-adj_quarters_kernel(const float* __restrict__ g, float* __restrict__ A, int N, int W)
+adj_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int N, int n, int k,
+                 int wc)
 {
-    const int u = blockIdx.x * blockDim.x + threadIdx.x;
-    const int tau = blockIdx.y;
+    constexpr int R = 1 << S;
+    constexpr int H = af_halo<S>();
+    constexpr int T = af_tile<S>();
+    extern __shared__ float sm[];
+    const int W = 2 * N;
+    const int tid = threadIdx.x;
     const int sq = blockIdx.z;                  // slice * 4 + quarter
-    const int q = sq & 3;
-    if (u >= W) return;
-    const float* gs = g + (size_t)(sq >> 2) * N * N;
-    float v = 0.0f;
-    if (u < N) {
-        switch (q) {
-            case 0: v = gs[(size_t)tau * N + u]; break;
-            case 1: v = gs[(size_t)tau * N + (N - 1 - u)]; break;
-            case 2: v = gs[(size_t)u * N + tau]; break;
-            default: v = gs[(size_t)(N - 1 - u) * N + tau]; break;
+    const int ko = k - S;                       // output level
+    const int g = blockIdx.y;                   // group: input rows g 2^S + j of level k
+    const int b = g >> ko, t = g & ((1 << ko) - 1);
+    const int xa = (b * t) << S;                // first column of every output row's range
+    const int x0 = xa + blockIdx.x * T;         // first output column (before the C t skew)
+    if (x0 >= W) return;                        // every output column x + C t >= W
+    const int xs = x0 - H;                      // column of shared column 0
+
+    // load the group's rows: shared row j, column p <-> input column xs + p
+    float* X = sm;
+    if constexpr (FROM_IMAGE) {
+        // level n = the quarter gradients of Eq. 22's index maps (g = t here, b = 0):
+        // v-: G[tau][u]  v+: G[tau][N-1-u]  h-: G[u][tau]  h+: G[N-1-u][tau], zero for u >= N
+        const float* gi = in + (size_t)(sq >> 2) * N * N;
+        const int q = sq & 3;
+        const int tau0 = g << S;
+        if (q < 2) {
+            const int x = xs + tid;
+            const bool ok = x >= 0 && x < N;
+            const int u = q == 0 ? x : N - 1 - x;
+#pragma unroll 4
+            for (int j = 0; j < R; ++j)
+                X[j * kAfPitch + tid] = ok ? gi[(size_t)(tau0 + j) * N + u] : 0.0f;
+        } else {
+            // columns of G: j fastest so that the 2^S rows' values of one u are adjacent
+#pragma unroll 4
+            for (int idx = tid; idx < R * kAfCols; idx += kAdjThreads) {
+                const int j = idx & (R - 1);
+                const int p = idx >> S;
+                const int x = xs + p;
+                const bool ok = x >= 0 && x < N;
+                const int u = q == 2 ? x : N - 1 - x;
+                X[j * kAfPitch + p] = ok ? gi[(size_t)u * N + tau0 + j] : 0.0f;
+            }
+        }
+    } else {
+        const float* rows = in + ((size_t)sq * N + ((size_t)g << S)) * W;
+        const int span = N + (1 << (n - k)) - 1;   // written length of every level-k row
+        const int x = xs + tid;
+#pragma unroll 4
+        for (int j = 0; j < R; ++j) {
+            const int lo = xa + b * j;          // b (2^S t + j)
+            const int hi = min(W, lo + span);
+            X[j * kAfPitch + tid] = (x >= lo && x < hi) ? rows[(size_t)j * W + x] : 0.0f;
         }
     }
-    A[((size_t)sq * N + tau) * W + u] = v;
+    __syncthreads();
+
+    // S transposed stages on the 2^S rows (slopes of the group alone), ping-ponging between
+    // the two shared buffers; row bc 2^(m-1) + tl of level m-1 from rows bl 2^m + 2tl and
+    // bl 2^m + 2tl + 1 of level m, bl = bc / 2.  Columns below 0 read as zero (they only
+    // feed halo columns).
+    float* cur = X;
+    float* nxt = X + R * kAfPitch;
+    const int p = tid;
+#pragma unroll
+    for (int m = S; m >= 1; --m) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int bc = r >> (m - 1), tl = r & ((1 << (m - 1)) - 1);
+            const float* a0 = cur + (((bc >> 1) << m) + 2 * tl) * kAfPitch;
+            const float* a1 = a0 + kAfPitch;
+            float o;
+            if ((bc & 1) == 0) {
+                o = a0[p] + a1[p];
+            } else {
+                const float y0 = p >= tl ? a0[p - tl] : 0.0f;
+                const float y1 = p >= tl + 1 ? a1[p - tl - 1] : 0.0f;
+                o = y0 + y1;
+            }
+            nxt[r * kAfPitch + p] = o;
+        }
+        __syncthreads();
+        float* sw = cur;
+        cur = nxt;
+        nxt = sw;
+    }
+
+    // shared row C = output strip b 2^S + C, slope t: column x = xs + p goes to x + C t,
+    // for x below the end of the written range xa + wc
+    if (p >= H) {
+        const int x = xs + p;
+        if (x < xa + wc) {
+            float* orow = out + ((size_t)sq * N + ((size_t)b << (S + ko)) + t) * W + x;
+#pragma unroll 4
+            for (int C = 0; C < R; ++C) {
+                const int v = x + C * t;
+                if (v < W) orow[((size_t)C << ko) * W + (size_t)C * t] = cur[C * kAfPitch + p];
+            }
+        }
+    }
 }
 
-// One transposed stage: level k (strips of 2^k rows) -> level k-1.  Rows are stored strip
-// after strip, row b 2^k + tau of level k holding A_k[b][tau].
-__global__ void __launch_bounds__(kAdjThreads)
-adj_stage_kernel(const float* __restrict__ in, float* __restrict__ out, int N, int W, int k)
+template <int S>
+cudaError_t set_af_attr()
 {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y;                   // output row at level k-1
-    const size_t base = (size_t)blockIdx.z * N * W;
-    if (v >= W) return;
-    const int h = 1 << (k - 1);
-    const int bc = r >> (k - 1);                // child strip at level k-1
-    const int t = r & (h - 1);
-    const int r0 = ((bc >> 1) << k) + 2 * t;    // A_k[bc / 2][2t]; r0 + 1 is A_k[bc / 2][2t + 1]
-    const float* a0 = in + base + (size_t)r0 * W;
-    const float* a1 = a0 + W;
-    float o;
-    if ((bc & 1) == 0) {
-        o = a0[v] + a1[v];
-    } else {
-        const float x0 = v >= t ? a0[v - t] : 0.0f;
-        const float x1 = v >= t + 1 ? a1[v - t - 1] : 0.0f;
-        o = x0 + x1;
-    }
-    out[base + (size_t)r * W + v] = o;
+    cudaError_t e = cudaFuncSetAttribute(adj_fused_kernel<S, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)af_smem<S>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(adj_fused_kernel<S, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)af_smem<S>());
+    return e;
+}
+
+template <int S>
+cudaError_t launch_af(const float* in, float* out, int N, int n, int k, int count, bool from_image,
+                      cudaStream_t st)
+{
+    const int W = 2 * N;
+    // written length of every output row: the last launch (level 0) writes all W columns
+    const int wc = k == S ? W : N + (1 << (n - k + S)) - 1;
+    const dim3 grid((wc + af_tile<S>() - 1) / af_tile<S>(), N >> S, 4 * count);
+    if (from_image)
+        adj_fused_kernel<S, true><<<grid, kAdjThreads, af_smem<S>(), st>>>(in, out, N, n, k, wc);
+    else
+        adj_fused_kernel<S, false><<<grid, kAdjThreads, af_smem<S>(), st>>>(in, out, N, n, k, wc);
+    return cudaGetLastError();
 }
 
 // Transposed resampling: every linogram sample's gradient into the four sinogram bins of
@@ -112,24 +223,42 @@ adj_resample_kernel(const float* __restrict__ lbar, float* __restrict__ pbar,
 
 }  // namespace
 
+cudaError_t prepare_adjoint_kernels()
+{
+    cudaError_t e = set_af_attr<1>();
+    if (e == cudaSuccess) e = set_af_attr<2>();
+    if (e == cudaSuccess) e = set_af_attr<3>();
+    if (e == cudaSuccess) e = set_af_attr<4>();
+    if (e == cudaSuccess) e = set_af_attr<5>();
+    return e;
+}
+
 cudaError_t launch_fht_adjoint(const fbp_plan_s* p, const float* img_grad, float* lin_grad,
                                float* scratch, int count, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    const int N = p->N, W = 2 * N, n = p->n;
-    // n stages after the quarter step: start in the buffer that makes the last stage land
-    // in lin_grad
+    const int N = p->N, n = p->n;
+    // ceil(n / 5) launches of at most five stages each, the larger shares first; start in
+    // the buffer that makes the last launch land in lin_grad
+    const int launches = (n + kAfMaxStages - 1) / kAfMaxStages;
     float* buf[2] = {lin_grad, scratch};
-    int cur = (n & 1) ? 1 : 0;
-    const dim3 blk(kAdjThreads);
-    adj_quarters_kernel<<<dim3((W + kAdjThreads - 1) / kAdjThreads, N, 4 * count), blk, 0, st>>>(
-        img_grad, buf[cur], N, W);
-    cudaError_t e = cudaGetLastError();
-    for (int k = n; k >= 1 && e == cudaSuccess; --k) {
-        adj_stage_kernel<<<dim3((W + kAdjThreads - 1) / kAdjThreads, N, 4 * count), blk, 0, st>>>(
-            buf[cur], buf[cur ^ 1], N, W, k);
+    int cur = (launches & 1) ? 0 : 1;
+    const float* src = img_grad;
+    int k = n;
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < launches && e == cudaSuccess; ++l) {
+        const int left = launches - l;
+        const int S = (k + left - 1) / left;
+        switch (S) {
+            case 1: e = launch_af<1>(src, buf[cur], N, n, k, count, l == 0, st); break;
+            case 2: e = launch_af<2>(src, buf[cur], N, n, k, count, l == 0, st); break;
+            case 3: e = launch_af<3>(src, buf[cur], N, n, k, count, l == 0, st); break;
+            case 4: e = launch_af<4>(src, buf[cur], N, n, k, count, l == 0, st); break;
+            default: e = launch_af<5>(src, buf[cur], N, n, k, count, l == 0, st); break;
+        }
+        src = buf[cur];
         cur ^= 1;
-        e = cudaGetLastError();
+        k -= S;
     }
     return e;
 }

@@ -14,6 +14,7 @@ namespace fbp {
 cudaError_t prepare_fht_kernels();
 cudaError_t prepare_iir_kernels();
 cudaError_t prepare_direct_kernels();
+cudaError_t prepare_adjoint_kernels();
 }
 
 namespace {
@@ -544,6 +545,7 @@ fbp_status fbp_plan(fbp_plan_t* out, int N, int K, int M, int batch,
         if (e == cudaSuccess) e = fbp::prepare_fht_kernels();
         if (e == cudaSuccess) e = fbp::prepare_iir_kernels();
         if (e == cudaSuccess) e = fbp::prepare_direct_kernels();
+        if (e == cudaSuccess) e = fbp::prepare_adjoint_kernels();
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->st_h2d, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->st_comp, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->st_d2h, cudaStreamNonBlocking);
