@@ -16,8 +16,8 @@
 //
 // Resampling, transposed.  Each linogram sample is w0 * lerp(row k0) + w1 * lerp(row k1)
 // (Eq. 14-15 with the float32 weights the forward kernels use); its transpose adds the
-// sample's gradient times the four bilinear weights into the sinogram gradient with
-// atomics (so the summation order, and the last bits, vary from run to run).
+// sample's gradient times the four bilinear weights into the sinogram gradient, gathered
+// per detector bin in a fixed order (reproducible bit for bit).
 #include "fbp_internal.h"
 
 namespace fbp {
@@ -85,31 +85,42 @@ adj_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int N, i
             const int x = xs + tid;
             const bool ok = x >= 0 && x < N;
             const int u = q == 0 ? x : N - 1 - x;
-#pragma unroll 4
-            for (int j = 0; j < R; ++j)
-                X[j * kAfPitch + tid] = ok ? gi[(size_t)(tau0 + j) * N + u] : 0.0f;
+            float v[R];                         // all of the rows' loads in flight at once
+#pragma unroll
+            for (int j = 0; j < R; ++j) v[j] = ok ? gi[(size_t)(tau0 + j) * N + u] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < R; ++j) X[j * kAfPitch + tid] = v[j];
         } else {
             // columns of G: j fastest so that the 2^S rows' values of one u are adjacent
-#pragma unroll 4
-            for (int idx = tid; idx < R * kAfCols; idx += kAdjThreads) {
+            float v[R];
+#pragma unroll
+            for (int it = 0; it < R; ++it) {
+                const int idx = tid + it * kAdjThreads;
                 const int j = idx & (R - 1);
-                const int p = idx >> S;
-                const int x = xs + p;
+                const int x = xs + (idx >> S);
                 const bool ok = x >= 0 && x < N;
                 const int u = q == 2 ? x : N - 1 - x;
-                X[j * kAfPitch + p] = ok ? gi[(size_t)u * N + tau0 + j] : 0.0f;
+                v[it] = ok ? gi[(size_t)u * N + tau0 + j] : 0.0f;
+            }
+#pragma unroll
+            for (int it = 0; it < R; ++it) {
+                const int idx = tid + it * kAdjThreads;
+                X[(idx & (R - 1)) * kAfPitch + (idx >> S)] = v[it];
             }
         }
     } else {
         const float* rows = in + ((size_t)sq * N + ((size_t)g << S)) * W;
         const int span = N + (1 << (n - k)) - 1;   // written length of every level-k row
         const int x = xs + tid;
-#pragma unroll 4
+        float v[R];
+#pragma unroll
         for (int j = 0; j < R; ++j) {
             const int lo = xa + b * j;          // b (2^S t + j)
             const int hi = min(W, lo + span);
-            X[j * kAfPitch + tid] = (x >= lo && x < hi) ? rows[(size_t)j * W + x] : 0.0f;
+            v[j] = (x >= lo && x < hi) ? rows[(size_t)j * W + x] : 0.0f;
         }
+#pragma unroll
+        for (int j = 0; j < R; ++j) X[j * kAfPitch + tid] = v[j];
     }
     __syncthreads();
 
@@ -149,7 +160,7 @@ adj_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int N, i
         const int x = xs + p;
         if (x < xa + wc) {
             float* orow = out + ((size_t)sq * N + ((size_t)b << (S + ko)) + t) * W + x;
-#pragma unroll 4
+#pragma unroll
             for (int C = 0; C < R; ++C) {
                 const int v = x + C * t;
                 if (v < W) orow[((size_t)C << ko) * W + (size_t)C * t] = cur[C * kAfPitch + p];
@@ -184,41 +195,97 @@ cudaError_t launch_af(const float* in, float* out, int N, int n, int k, int coun
     return cudaGetLastError();
 }
 
-// Transposed resampling: every linogram sample's gradient into the four sinogram bins of
-// its bilinear interpolation (same fixed-point positions and float32 weights as the forward
-// resampling).  Samples of value zero (all of them outside the trapezoid) add nothing.
-__global__ void __launch_bounds__(kAdjThreads)
+// Transposed resampling as a gather: thread = 4 consecutive bins j0..j0+3 of sinogram row
+// k of one slice.  The linogram rows whose resampling reads row k (as their lower angle row
+// k0 with weight w0, as their upper row k0 + 1 with weight w1, or as row 0 with the detector
+// mirrored, m' = M - 1 - m, past the last angle) are listed per row at plan time.  For each
+// such row the thread walks the columns c whose detector position m(c) = a c + b (32.32
+// fixed point, monotone in c, |a| <= 1) falls in [j0 - 1, j0 + 4), found from a float
+// estimate widened by one column on each side and then tested exactly, and adds w L-bar[c]
+// (1 - f) to bin floor(m) and w L-bar[c] f to bin floor(m) + 1 where those are its own:
+// the same positions and float32 weights as the forward resampling.  No atomics: the order
+// of the additions is fixed (rows in table order, c ascending), so the result is
+// reproducible bit for bit.
+constexpr int kRsEnt = 32;                      // reader rows staged per round
+constexpr int kRsBins = 4;                      // bins per thread (acc0 .. acc3)
+constexpr int kRsWin = 12;                      // columns a thread reads per reader row
+
+__global__ void __launch_bounds__(kAdjThreads, 1)
 adj_resample_kernel(const float* __restrict__ lbar, float* __restrict__ pbar,
-                    const RowGeom* __restrict__ geom, int N, int K, int M)
+                    const RowGeom* __restrict__ geom, const int* __restrict__ readers, int N,
+                    int K, int M)
 {
-    const int W = 2 * N;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int qi = blockIdx.y;                  // q * N + i
+    __shared__ long long ea[kRsEnt], eb[kRsEnt];    // m(c) = ea c + eb (mirror folded in)
+    __shared__ float efi[kRsEnt], efb[kRsEnt];      // 1 / a and b in float, for the estimate
+    __shared__ float ew[kRsEnt];
+    __shared__ int eq[kRsEnt];
+    const int k = blockIdx.y;
     const int s = blockIdx.z;
-    if (c >= W) return;
-    const float val = lbar[((size_t)s * 4 * N + qi) * W + c];
-    if (val == 0.0f) return;
-    const RowGeom gm = geom[qi];
-    float* ps = pbar + (size_t)s * K * M;
-    const long long m = gm.b_fx + gm.a_fx * (long long)c;
-    const int j = (int)(m >> kFixBits);
-    const float f = __uint2float_rn((unsigned)m) * 0x1p-32f;
-    float* ra = ps + (size_t)gm.k0 * M;
-    const float va = gm.w0 * val;               // gradient of the k0 lerp
-    if (j >= 0 && j < M) atomicAdd(ra + j, va * (1.0f - f));
-    if (j + 1 >= 0 && j + 1 < M) atomicAdd(ra + j + 1, va * f);
-    const float vb = gm.w1 * val;
-    if (!gm.wrap) {
-        float* rb = ra + M;
-        if (j >= 0 && j < M) atomicAdd(rb + j, vb * (1.0f - f));
-        if (j + 1 >= 0 && j + 1 < M) atomicAdd(rb + j + 1, vb * f);
-    } else {                                    // row 0, detector mirrored: m' = M-1-m
-        const long long mm = ((long long)(M - 1) << kFixBits) - m;
-        const int jm = (int)(mm >> kFixBits);
-        const float fm = __uint2float_rn((unsigned)mm) * 0x1p-32f;
-        if (jm >= 0 && jm < M) atomicAdd(ps + jm, vb * (1.0f - fm));
-        if (jm + 1 >= 0 && jm + 1 < M) atomicAdd(ps + jm + 1, vb * fm);
+    const int W = 2 * N;
+    const int j0 = (blockIdx.x * kAdjThreads + threadIdx.x) * kRsBins;
+    const float* ls = lbar + (size_t)s * 4 * N * W;
+    float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f, acc3 = 0.0f;     // bins j0 .. j0 + 3
+    const int r0 = readers[k], r1 = readers[k + 1];
+    for (int rb = r0; rb < r1; rb += kRsEnt) {
+        const int ne = min(kRsEnt, r1 - rb);
+        __syncthreads();                        // previous round's tables are read
+        if (threadIdx.x < ne) {
+            const int code = readers[rb + threadIdx.x];
+            const int qi = code >> 2, slot = code & 3;
+            const RowGeom gm = geom[qi];
+            long long a = gm.a_fx, b = gm.b_fx;
+            if (slot == 2) {                    // m' = (M - 1) - m = -a c + ((M - 1) - b)
+                b = ((long long)(M - 1) << kFixBits) - b;
+                a = -a;
+            }
+            ea[threadIdx.x] = a;
+            eb[threadIdx.x] = b;
+            efi[threadIdx.x] = __fdividef(1.0f, (float)a * 0x1p-32f);   // estimate only
+            efb[threadIdx.x] = (float)b * 0x1p-32f;
+            ew[threadIdx.x] = slot == 0 ? gm.w0 : gm.w1;
+            eq[threadIdx.x] = qi;
+        }
+        __syncthreads();
+        if (j0 >= M) continue;
+        for (int e = 0; e < ne; ++e) {
+            const float fi = efi[e], fb = efb[e];
+            // columns with m(c) in [j0 - 1, j0 + 4), estimated, plus one on each side: at
+            // most 5 / |a| + 3 <= 11 of them (|a| >= 1 / sqrt 2), loaded all at once
+            const float c1 = ((float)(j0 - 1) - fb) * fi;
+            const float c2 = ((float)(j0 + kRsBins) - fb) * fi;
+            const float clo = fmaxf(fminf(c1, c2) - 1.0f, 0.0f);
+            const float chi = fminf(fmaxf(c1, c2) + 1.0f, (float)(W - 1));
+            if (clo > chi) continue;
+            const int cs = (int)clo, ce = (int)chi;
+            const long long a = ea[e];
+            const float w = ew[e];
+            const float* lr = ls + (size_t)eq[e] * W + cs;
+            float lv[kRsWin];
+#pragma unroll
+            for (int u = 0; u < kRsWin; ++u) lv[u] = cs + u <= ce ? lr[u] : 0.0f;
+            const long long mb = eb[e] + a * (long long)cs;
+#pragma unroll
+            for (int u = 0; u < kRsWin; ++u) {
+                const long long m = mb + a * u;
+                const int d = (int)(m >> kFixBits) - j0;       // bin floor(m) - j0
+                if (cs + u > ce || d < -1 || d >= kRsBins) continue;
+                const float f = __uint2float_rn((unsigned)m) * 0x1p-32f;
+                const float v = w * lv[u];
+                const float v0 = v * (1.0f - f), v1 = v * f;     // to bins d and d + 1
+                if (d == -1) acc0 += v1;
+                else if (d == 0) { acc0 += v0; acc1 += v1; }
+                else if (d == 1) { acc1 += v0; acc2 += v1; }
+                else if (d == 2) { acc2 += v0; acc3 += v1; }
+                else acc3 += v0;
+            }
+        }
     }
+    if (j0 >= M) return;
+    float* out = pbar + ((size_t)s * K + k) * M + j0;
+    out[0] = acc0;
+    if (j0 + 1 < M) out[1] = acc1;
+    if (j0 + 2 < M) out[2] = acc2;
+    if (j0 + 3 < M) out[3] = acc3;
 }
 
 }  // namespace
@@ -267,10 +334,9 @@ cudaError_t launch_resample_adjoint(const fbp_plan_s* p, const float* lin_grad, 
                                     int count, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(filt_grad, 0, (size_t)count * p->K * p->M * sizeof(float), st);
-    if (e != cudaSuccess) return e;
-    adj_resample_kernel<<<dim3((2 * p->N + kAdjThreads - 1) / kAdjThreads, 4 * p->N, count),
-                          kAdjThreads, 0, st>>>(lin_grad, filt_grad, p->d_geom, p->N, p->K, p->M);
+    const int per_cta = kAdjThreads * kRsBins;
+    adj_resample_kernel<<<dim3((p->M + per_cta - 1) / per_cta, p->K, count), kAdjThreads, 0, st>>>(
+        lin_grad, filt_grad, p->d_geom, p->d_readers, p->N, p->K, p->M);
     return cudaGetLastError();
 }
 

@@ -298,6 +298,25 @@ std::vector<fbp::RowGeom> build_geometry(int N, int K, int M)
     return g;
 }
 
+// Per sinogram row, the linogram rows whose resampling reads it (Eq. 14-15: row (q, i)
+// interpolates between angle rows k0 and k0 + 1, or k0 and row 0 mirrored past the last
+// angle), as a CSR table for the transposed resampling.
+std::vector<int> build_readers(const std::vector<fbp::RowGeom>& geo, int K)
+{
+    std::vector<std::vector<int>> rows(K);
+    for (size_t qi = 0; qi < geo.size(); ++qi) {
+        const fbp::RowGeom& g = geo[qi];
+        rows[g.k0].push_back((int)qi * 4 + 0);
+        if (g.wrap) rows[0].push_back((int)qi * 4 + 2);
+        else rows[g.k0 + 1].push_back((int)qi * 4 + 1);
+    }
+    std::vector<int> out(K + 1);
+    out[0] = K + 1;
+    for (int k = 0; k < K; ++k) out[k + 1] = out[k] + (int)rows[k].size();
+    for (int k = 0; k < K; ++k) out.insert(out.end(), rows[k].begin(), rows[k].end());
+    return out;
+}
+
 int ilog2(int v)
 {
     int n = 0;
@@ -534,13 +553,17 @@ fbp_status fbp_plan(fbp_plan_t* out, int N, int K, int M, int batch,
         const double th = k * M_PI / K;
         trig[k] = make_float2((float)cos(th), (float)sin(th));
     }
+    const std::vector<int> readers = build_readers(geo, K);
     cudaError_t e = cudaMalloc(&p->d_geom, geo.size() * sizeof(fbp::RowGeom));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_trig, trig.size() * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_readers, readers.size() * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
     if (e != cudaSuccess) st = FBP_ERR_OOM;
     if (st == FBP_OK) {
         e = cudaMemcpy(p->d_geom, geo.data(), geo.size() * sizeof(fbp::RowGeom), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(p->d_trig, trig.data(), trig.size() * sizeof(float2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_readers, readers.data(), readers.size() * sizeof(int), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
         if (e == cudaSuccess) e = fbp::prepare_fht_kernels();
         if (e == cudaSuccess) e = fbp::prepare_iir_kernels();
@@ -577,6 +600,7 @@ fbp_status fbp_plan_destroy(fbp_plan_t p)
     if (p->adj_ws) cudaFree(p->adj_ws);
     if (p->d_geom) cudaFree(p->d_geom);
     if (p->d_trig) cudaFree(p->d_trig);
+    if (p->d_readers) cudaFree(p->d_readers);
     if (p->d_status) cudaFree(p->d_status);
     cudaStream_t ss[3] = {p->st_h2d, p->st_comp, p->st_d2h};
     for (cudaStream_t s : ss)

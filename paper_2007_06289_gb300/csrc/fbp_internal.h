@@ -65,6 +65,9 @@ struct fbp_plan_s {
     fbp::IirParams iir;
     fbp::RowGeom* d_geom;   // [4][N]
     float2* d_trig;         // [K] (cos, sin) for the direct comparator
+    int* d_readers;         // per sinogram row k: the linogram rows whose resampling reads
+                            // it, CSR: [K + 1] offsets, then entries 4 (q N + i) + slot
+                            // (0: as row k0, 1: as row k0 + 1, 2: as row 0 mirrored)
     int* d_status;          // device status word
     // workspace
     void* ws;
