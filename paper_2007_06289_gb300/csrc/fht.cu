@@ -492,12 +492,18 @@ pass1_kernel(Pass1Args a)
         const int M = a.M;
         const int pitch = a.pitch;
         constexpr int kS = 4;
-        // start every row of this warp on its way into L2 before gathering any of them
-        for (int j = warp; j < R; j += NWARPS) {
+        // each warp takes RPW consecutive rows, which mostly share their angle rows (L1
+        // reuse); start all of them on their way into L2 before gathering any
+        constexpr int RPW = R >= NWARPS ? R / NWARPS : 1;
+        for (int jj = 0; jj < RPW; ++jj) {
+            const int j = warp * RPW + jj;
+            if (j >= R) break;
             const int i = bi * R + j;
             if (c0 <= N - 1 + i) prefetch_tile_row<WB>(pt, pitch, M, a.geom[q * N + i], c0, lane);
         }
-        for (int j = warp; j < R; j += NWARPS) {
+        for (int jj = 0; jj < RPW; ++jj) {
+            const int j = warp * RPW + jj;
+            if (j >= R) break;
             const int i = bi * R + j;
             const int limit = N - 1 + i;
             float* row = buf + j * PITCH + lane;
