@@ -158,12 +158,14 @@ fbp_status fbp_fht_backproject_adjoint(fbp_plan_t plan, const float* d_img_grad,
 fbp_status fbp_hough_project(fbp_plan_t plan, const float* d_img, float* d_lin, void* stream);
 
 /* L^T: linogram gradient [batch][4][N][2N] -> filtered-sinogram gradient [batch][K][M]
- * (overwritten): each sample's gradient times its four bilinear weights, added with
- * float atomics (the last bits depend on the order of the additions). */
+ * (every entry overwritten): each sample's gradient times its four bilinear weights (the
+ * forward's float32 weights and fixed-point positions), gathered per detector bin in a fixed
+ * order, no atomics: bit-reproducible from run to run. */
 fbp_status fbp_resample_st_adjoint(fbp_plan_t plan, const float* d_lin_grad,
                                    float* d_filt_grad, void* stream);
 
-/* (H L F)^T = F L^T H^T: image gradient [batch][N][N] -> sinogram gradient [batch][K][M]. */
+/* (H L F)^T = F L^T H^T: image gradient [batch][N][N] -> sinogram gradient [batch][K][M]
+ * (bit-reproducible: all three steps are). */
 fbp_status fbp_reconstruct_adjoint(fbp_plan_t plan, const float* d_img_grad,
                                    float* d_sino_grad, void* stream);
 
