@@ -16,6 +16,8 @@
 // followed by its biases [co].
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "fbp_internal.h"
 
 namespace fbp {
@@ -444,17 +446,27 @@ Ws carve(void* ws, int N, int batch)
     return w;
 }
 
+constexpr int kMaxCnnDevices = 64;
+
 template <bool BIAS, bool RELU, bool MASK>
 cudaError_t launch_conv32(const bf16* in, const bf16* wt, const float* bias, const bf16* mask,
                           bf16* out, int N, int batch, int sms, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(cnn_conv32_kernel<BIAS, RELU, MASK>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)kConvSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
+    // the shared-memory opt-in is per device: done once for each device this runs on
+    static std::mutex lock;
+    static bool done[kMaxCnnDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxCnnDevices) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> g(lock);
+        if (!done[dev]) {
+            e = cudaFuncSetAttribute(cnn_conv32_kernel<BIAS, RELU, MASK>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
+            if (e != cudaSuccess) return e;
+            done[dev] = true;
+        }
     }
     const long long tiles = (long long)(N / kT2) * (N / kT2) * batch;
     const int grid = (int)(tiles < 3LL * sms ? tiles : 3LL * sms);
