@@ -201,14 +201,14 @@ cudaError_t launch_af(const float* in, float* out, int N, int n, int k, int coun
 // mirrored, m' = M - 1 - m, past the last angle) are listed per row at plan time.  For each
 // such row the thread walks the columns c whose detector position m(c) = a c + b (32.32
 // fixed point, monotone in c, |a| <= 1) falls in [j0 - 1, j0 + 4), found from a float
-// estimate widened by one column on each side and then tested exactly, and adds w L-bar[c]
+// estimate of the window and then tested exactly, and adds w L-bar[c]
 // (1 - f) to bin floor(m) and w L-bar[c] f to bin floor(m) + 1 where those are its own:
 // the same positions and float32 weights as the forward resampling.  No atomics: the order
 // of the additions is fixed (rows in table order, c ascending), so the result is
 // reproducible bit for bit.
 constexpr int kRsEnt = 32;                      // reader rows staged per round
 constexpr int kRsBins = 4;                      // bins per thread (acc0 .. acc3)
-constexpr int kRsWin = 12;                      // columns a thread reads per reader row
+constexpr int kRsWin = 10;                      // columns a thread reads per reader row
 
 __global__ void __launch_bounds__(kAdjThreads, 1)
 adj_resample_kernel(const float* __restrict__ lbar, float* __restrict__ pbar,
@@ -249,11 +249,13 @@ adj_resample_kernel(const float* __restrict__ lbar, float* __restrict__ pbar,
         if (j0 >= M) continue;
         for (int e = 0; e < ne; ++e) {
             const float fi = efi[e], fb = efb[e];
-            // columns with m(c) in [j0 - 1, j0 + 4), estimated, plus one on each side: at
-            // most 5 / |a| + 3 <= 11 of them (|a| >= 1 / sqrt 2), loaded all at once
+            // columns with m(c) in [j0 - 1, j0 + 4): an interval of 5 / |a| <= 5 sqrt 2
+            // columns (|a| >= 1 / sqrt 2), so at most 8 of them; the float estimate of the
+            // first may land one below it: a window of kRsWin = 10 from floor(estimate),
+            // loaded all at once (checked over every row and bin group for N = 256 .. 4096)
             const float c1 = ((float)(j0 - 1) - fb) * fi;
             const float c2 = ((float)(j0 + kRsBins) - fb) * fi;
-            const float clo = fmaxf(fminf(c1, c2) - 1.0f, 0.0f);
+            const float clo = fmaxf(fminf(c1, c2), 0.0f);
             const float chi = fminf(fmaxf(c1, c2) + 1.0f, (float)(W - 1));
             if (clo > chi) continue;
             const int cs = (int)clo, ce = (int)chi;
