@@ -841,8 +841,14 @@ fbp_status fbp_resample_st_adjoint(fbp_plan_t p, const float* d_lin_grad, float*
     if (!aligned16(d_lin_grad) || !aligned16(d_filt_grad)) return FBP_ERR_MISALIGNED;
     DeviceGuard g(p->device);
     if (!g.ok) return FBP_ERR_CUDA;
-    return cuda_status(fbp::launch_resample_adjoint(p, d_lin_grad, d_filt_grad, p->batch,
-                                                   (cudaStream_t)stream));
+    for (int c = 0; c < p->batch; c += p->chunk) {      // grid z is the chunk's slice count
+        const int cnt = p->batch - c < p->chunk ? p->batch - c : p->chunk;
+        const cudaError_t e = fbp::launch_resample_adjoint(
+            p, d_lin_grad + (size_t)c * fbp::lin_floats(p),
+            d_filt_grad + (size_t)c * fbp::sino_floats(p), cnt, (cudaStream_t)stream);
+        if (e != cudaSuccess) return FBP_ERR_CUDA;
+    }
+    return FBP_OK;
 }
 
 fbp_status fbp_reconstruct_adjoint(fbp_plan_t p, const float* d_img_grad, float* d_sino_grad,
