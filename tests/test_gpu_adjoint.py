@@ -44,6 +44,20 @@ def test_backprojection_adjoint_bit_exact(fbp, torch, N):
         np.testing.assert_array_equal(got[b], want)
 
 
+@pytest.mark.parametrize("N", [1024, 2048])
+def test_backprojection_adjoint_bit_exact_large(fbp, torch, N):
+    # N = 1024: two launches of five stages; N = 2048: three launches (4 + 4 + 3), the
+    # middle one reading and writing partially written level arrays
+    rng = np.random.default_rng(N + 7)
+    g = rng.normal(size=(1, N, N)).astype(np.float32)
+    K, M = phantoms.geometry_for(N)
+    plan = fbp.fbp_plan(N, K, M, 1)
+    lin = torch.full(plan.lin_shape, float("nan"), device="cuda")
+    fbp.fbp_fht_backproject_adjoint(plan, dev(torch, g), lin)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(lin.cpu().numpy()[0], oracle.fht_backproject_adjoint(g[0]))
+
+
 def test_backprojection_adjoint_integer_inputs_exact(fbp, torch):
     N = 256
     rng = np.random.default_rng(9)
