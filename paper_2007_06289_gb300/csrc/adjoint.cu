@@ -195,46 +195,52 @@ cudaError_t launch_af(const float* in, float* out, int N, int n, int k, int coun
     return cudaGetLastError();
 }
 
-// Transposed resampling as a gather: thread = 4 consecutive bins j0..j0+3 of sinogram row
-// k of one slice.  The linogram rows whose resampling reads row k (as their lower angle row
-// k0 with weight w0, as their upper row k0 + 1 with weight w1, or as row 0 with the detector
-// mirrored, m' = M - 1 - m, past the last angle) are listed per row at plan time.  For each
-// such row the thread walks the columns c whose detector position m(c) = a c + b (32.32
-// fixed point, monotone in c, |a| <= 1) falls in [j0 - 1, j0 + 4), found from a float
-// estimate of the window and then tested exactly, and adds w L-bar[c]
-// (1 - f) to bin floor(m) and w L-bar[c] f to bin floor(m) + 1 where those are its own:
-// the same positions and float32 weights as the forward resampling.  No atomics: the order
-// of the additions is fixed (rows in table order, c ascending), so the result is
-// reproducible bit for bit.
+// Transposed resampling as a gather: a CTA owns kRsRows consecutive sinogram rows of one
+// slice, a thread 4 consecutive bins j0..j0+3 of each.  The plan lists the linogram rows
+// whose resampling reads the group's rows (each with its weight into every row of the
+// group: w0 into its angle row k0, w1 into k0 + 1, or into row 0 with the detector
+// mirrored, m' = M - 1 - m, past the last angle).  For each listed row the thread walks the
+// columns c whose detector position m(c) = a c + b (32.32 fixed point, monotone in c,
+// |a| <= 1) falls in [j0 - 1, j0 + 4), tests each exactly, and sums L-bar[c] (1 - f) into
+// bin floor(m) and L-bar[c] f into bin floor(m) + 1 where those are its own (the forward
+// resampling's positions and float32 fractions); the row's sums then go to every group row
+// it reads, times that row's weight.  Computing each linogram row's sums once for both of
+// its angle rows is what grouping the rows saves.  No atomics: the order of the additions
+// is fixed (table order, c ascending), so the result is reproducible bit for bit.
 constexpr int kRsEnt = 32;                      // reader rows staged per round
-constexpr int kRsBins = 4;                      // bins per thread (acc0 .. acc3)
+constexpr int kRsBins = 4;                      // bins per thread (s0 .. s3)
 constexpr int kRsWin = 10;                      // columns a thread reads per reader row
 
 __global__ void __launch_bounds__(kAdjThreads, 1)
 adj_resample_kernel(const float* __restrict__ lbar, float* __restrict__ pbar,
-                    const RowGeom* __restrict__ geom, const int* __restrict__ readers, int N,
-                    int K, int M)
+                    const RowGeom* __restrict__ geom, const int* __restrict__ rptr,
+                    const ReaderEntry* __restrict__ rent, int N, int K, int M)
 {
     __shared__ long long ea[kRsEnt], eb[kRsEnt];    // m(c) = ea c + eb (mirror folded in)
     __shared__ float efi[kRsEnt], efb[kRsEnt];      // 1 / a and b in float, for the estimate
-    __shared__ float ew[kRsEnt];
+    __shared__ float4 ew[kRsEnt];                   // weights into the group's rows
     __shared__ int eq[kRsEnt];
-    const int k = blockIdx.y;
+    static_assert(kRsRows == 4, "weights staged as float4");
+    const int grp = blockIdx.y;
     const int s = blockIdx.z;
     const int W = 2 * N;
     const int j0 = (blockIdx.x * kAdjThreads + threadIdx.x) * kRsBins;
     const float* ls = lbar + (size_t)s * 4 * N * W;
-    float acc0 = 0.0f, acc1 = 0.0f, acc2 = 0.0f, acc3 = 0.0f;     // bins j0 .. j0 + 3
-    const int r0 = readers[k], r1 = readers[k + 1];
+    float acc[kRsRows][kRsBins];
+#pragma unroll
+    for (int r = 0; r < kRsRows; ++r)
+#pragma unroll
+        for (int b = 0; b < kRsBins; ++b) acc[r][b] = 0.0f;
+    const int r0 = rptr[grp], r1 = rptr[grp + 1];
     for (int rb = r0; rb < r1; rb += kRsEnt) {
         const int ne = min(kRsEnt, r1 - rb);
         __syncthreads();                        // previous round's tables are read
         if (threadIdx.x < ne) {
-            const int code = readers[rb + threadIdx.x];
-            const int qi = code >> 2, slot = code & 3;
+            const ReaderEntry en = rent[rb + threadIdx.x];
+            const int qi = en.code >> 1;
             const RowGeom gm = geom[qi];
             long long a = gm.a_fx, b = gm.b_fx;
-            if (slot == 2) {                    // m' = (M - 1) - m = -a c + ((M - 1) - b)
+            if (en.code & 1) {                  // m' = (M - 1) - m = -a c + ((M - 1) - b)
                 b = ((long long)(M - 1) << kFixBits) - b;
                 a = -a;
             }
@@ -242,7 +248,7 @@ adj_resample_kernel(const float* __restrict__ lbar, float* __restrict__ pbar,
             eb[threadIdx.x] = b;
             efi[threadIdx.x] = __fdividef(1.0f, (float)a * 0x1p-32f);   // estimate only
             efb[threadIdx.x] = (float)b * 0x1p-32f;
-            ew[threadIdx.x] = slot == 0 ? gm.w0 : gm.w1;
+            ew[threadIdx.x] = make_float4(en.w[0], en.w[1], en.w[2], en.w[3]);
             eq[threadIdx.x] = qi;
         }
         __syncthreads();
@@ -260,34 +266,46 @@ adj_resample_kernel(const float* __restrict__ lbar, float* __restrict__ pbar,
             if (clo > chi) continue;
             const int cs = (int)clo, ce = (int)chi;
             const long long a = ea[e];
-            const float w = ew[e];
             const float* lr = ls + (size_t)eq[e] * W + cs;
             float lv[kRsWin];
 #pragma unroll
             for (int u = 0; u < kRsWin; ++u) lv[u] = cs + u <= ce ? lr[u] : 0.0f;
             const long long mb = eb[e] + a * (long long)cs;
+            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;    // bins j0 .. j0 + 3
 #pragma unroll
             for (int u = 0; u < kRsWin; ++u) {
                 const long long m = mb + a * u;
                 const int d = (int)(m >> kFixBits) - j0;       // bin floor(m) - j0
                 if (cs + u > ce || d < -1 || d >= kRsBins) continue;
                 const float f = __uint2float_rn((unsigned)m) * 0x1p-32f;
-                const float v = w * lv[u];
-                const float v0 = v * (1.0f - f), v1 = v * f;     // to bins d and d + 1
-                if (d == -1) acc0 += v1;
-                else if (d == 0) { acc0 += v0; acc1 += v1; }
-                else if (d == 1) { acc1 += v0; acc2 += v1; }
-                else if (d == 2) { acc2 += v0; acc3 += v1; }
-                else acc3 += v0;
+                const float v0 = lv[u] * (1.0f - f), v1 = lv[u] * f;   // to bins d, d + 1
+                if (d == -1) s0 += v1;
+                else if (d == 0) { s0 += v0; s1 += v1; }
+                else if (d == 1) { s1 += v0; s2 += v1; }
+                else if (d == 2) { s2 += v0; s3 += v1; }
+                else s3 += v0;
+            }
+            const float4 w = ew[e];
+            const float wr[kRsRows] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int r = 0; r < kRsRows; ++r) {
+                acc[r][0] = fmaf(wr[r], s0, acc[r][0]);
+                acc[r][1] = fmaf(wr[r], s1, acc[r][1]);
+                acc[r][2] = fmaf(wr[r], s2, acc[r][2]);
+                acc[r][3] = fmaf(wr[r], s3, acc[r][3]);
             }
         }
     }
     if (j0 >= M) return;
-    float* out = pbar + ((size_t)s * K + k) * M + j0;
-    out[0] = acc0;
-    if (j0 + 1 < M) out[1] = acc1;
-    if (j0 + 2 < M) out[2] = acc2;
-    if (j0 + 3 < M) out[3] = acc3;
+#pragma unroll
+    for (int r = 0; r < kRsRows; ++r) {
+        const int k = grp * kRsRows + r;
+        if (k >= K) break;
+        float* out = pbar + ((size_t)s * K + k) * M + j0;
+#pragma unroll
+        for (int b = 0; b < kRsBins; ++b)
+            if (j0 + b < M) out[b] = acc[r][b];
+    }
 }
 
 }  // namespace
@@ -337,8 +355,9 @@ cudaError_t launch_resample_adjoint(const fbp_plan_s* p, const float* lin_grad, 
 {
     if (count <= 0) return cudaSuccess;
     const int per_cta = kAdjThreads * kRsBins;
-    adj_resample_kernel<<<dim3((p->M + per_cta - 1) / per_cta, p->K, count), kAdjThreads, 0, st>>>(
-        lin_grad, filt_grad, p->d_geom, p->d_readers, p->N, p->K, p->M);
+    const dim3 grid((p->M + per_cta - 1) / per_cta, (p->K + kRsRows - 1) / kRsRows, count);
+    adj_resample_kernel<<<grid, kAdjThreads, 0, st>>>(lin_grad, filt_grad, p->d_geom, p->d_readers,
+                                                      p->d_reader_ent, p->N, p->K, p->M);
     return cudaGetLastError();
 }
 

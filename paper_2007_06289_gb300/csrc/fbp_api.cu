@@ -298,23 +298,51 @@ std::vector<fbp::RowGeom> build_geometry(int N, int K, int M)
     return g;
 }
 
-// Per sinogram row, the linogram rows whose resampling reads it (Eq. 14-15: row (q, i)
-// interpolates between angle rows k0 and k0 + 1, or k0 and row 0 mirrored past the last
-// angle), as a CSR table for the transposed resampling.
-std::vector<int> build_readers(const std::vector<fbp::RowGeom>& geo, int K)
+// Transposed-resampling table: per group of kRsRows sinogram rows, the linogram rows whose
+// resampling reads any row of the group (Eq. 14-15: row (q, i) interpolates between angle
+// rows k0 and k0 + 1 with weights w0 and w1, or, past the last angle, between k0 and row 0
+// with the detector mirrored), each with its weight into every row of the group.  A row
+// whose two angle rows fall in different groups appears in both.  Entries are in (q, i)
+// order, mirrored reads after the direct ones of group 0.
+struct ReaderTable {
+    std::vector<int> ptr;
+    std::vector<fbp::ReaderEntry> ent;
+};
+
+ReaderTable build_readers(const std::vector<fbp::RowGeom>& geo, int K)
 {
-    std::vector<std::vector<int>> rows(K);
+    const int R = fbp::kRsRows;
+    const int groups = (K + R - 1) / R;
+    std::vector<std::vector<fbp::ReaderEntry>> per(groups);
+    std::vector<fbp::ReaderEntry> mirrored;
+    auto add = [&](int row, int code, float w) {
+        std::vector<fbp::ReaderEntry>& v = per[row / R];
+        if (v.empty() || v.back().code != code) {
+            fbp::ReaderEntry e{code, {}};
+            v.push_back(e);
+        }
+        v.back().w[row % R] += w;
+    };
     for (size_t qi = 0; qi < geo.size(); ++qi) {
         const fbp::RowGeom& g = geo[qi];
-        rows[g.k0].push_back((int)qi * 4 + 0);
-        if (g.wrap) rows[0].push_back((int)qi * 4 + 2);
-        else rows[g.k0 + 1].push_back((int)qi * 4 + 1);
+        add(g.k0, (int)qi * 2, g.w0);
+        if (!g.wrap) {
+            add(g.k0 + 1, (int)qi * 2, g.w1);
+        } else {
+            fbp::ReaderEntry e{(int)qi * 2 + 1, {}};
+            e.w[0] = g.w1;
+            mirrored.push_back(e);
+        }
     }
-    std::vector<int> out(K + 1);
-    out[0] = K + 1;
-    for (int k = 0; k < K; ++k) out[k + 1] = out[k] + (int)rows[k].size();
-    for (int k = 0; k < K; ++k) out.insert(out.end(), rows[k].begin(), rows[k].end());
-    return out;
+    per[0].insert(per[0].end(), mirrored.begin(), mirrored.end());
+    ReaderTable t;
+    t.ptr.resize(groups + 1);
+    t.ptr[0] = 0;
+    for (int gi = 0; gi < groups; ++gi) {
+        t.ptr[gi + 1] = t.ptr[gi] + (int)per[gi].size();
+        t.ent.insert(t.ent.end(), per[gi].begin(), per[gi].end());
+    }
+    return t;
 }
 
 int ilog2(int v)
@@ -553,17 +581,23 @@ fbp_status fbp_plan(fbp_plan_t* out, int N, int K, int M, int batch,
         const double th = k * M_PI / K;
         trig[k] = make_float2((float)cos(th), (float)sin(th));
     }
-    const std::vector<int> readers = build_readers(geo, K);
+    const ReaderTable readers = build_readers(geo, K);
     cudaError_t e = cudaMalloc(&p->d_geom, geo.size() * sizeof(fbp::RowGeom));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_trig, trig.size() * sizeof(float2));
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_readers, readers.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_readers, readers.ptr.size() * sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&p->d_reader_ent, readers.ent.size() * sizeof(fbp::ReaderEntry));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
     if (e != cudaSuccess) st = FBP_ERR_OOM;
     if (st == FBP_OK) {
         e = cudaMemcpy(p->d_geom, geo.data(), geo.size() * sizeof(fbp::RowGeom), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(p->d_trig, trig.data(), trig.size() * sizeof(float2), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
-            e = cudaMemcpy(p->d_readers, readers.data(), readers.size() * sizeof(int), cudaMemcpyHostToDevice);
+            e = cudaMemcpy(p->d_readers, readers.ptr.data(), readers.ptr.size() * sizeof(int),
+                           cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_reader_ent, readers.ent.data(),
+                           readers.ent.size() * sizeof(fbp::ReaderEntry), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
         if (e == cudaSuccess) e = fbp::prepare_fht_kernels();
         if (e == cudaSuccess) e = fbp::prepare_iir_kernels();
@@ -601,6 +635,7 @@ fbp_status fbp_plan_destroy(fbp_plan_t p)
     if (p->d_geom) cudaFree(p->d_geom);
     if (p->d_trig) cudaFree(p->d_trig);
     if (p->d_readers) cudaFree(p->d_readers);
+    if (p->d_reader_ent) cudaFree(p->d_reader_ent);
     if (p->d_status) cudaFree(p->d_status);
     cudaStream_t ss[3] = {p->st_h2d, p->st_comp, p->st_d2h};
     for (cudaStream_t s : ss)

@@ -56,6 +56,18 @@ constexpr int kIirMaxWarps = 32;   // warps per row, so M <= 32 * 32 * 23
 
 }  // namespace fbp
 
+namespace fbp {
+// Transposed resampling table.  Sinogram rows are taken kRsRows at a time; an entry is one
+// linogram row whose resampling reads rows of the group: code = 2 (q N + i) + mirrored
+// (1: the row-0 read past the last angle, detector mirrored), w[r] = its weight into group
+// row r (w0 for its angle row k0, w1 for k0 + 1, 0 for the others).
+constexpr int kRsRows = 4;
+struct ReaderEntry {
+    int code;
+    float w[kRsRows];
+};
+}  // namespace fbp
+
 struct fbp_plan_s {
     int N, K, M, batch;
     int n, n1, n2;          // log2 N, Hough stages in pass 1 and pass 2
@@ -65,9 +77,9 @@ struct fbp_plan_s {
     fbp::IirParams iir;
     fbp::RowGeom* d_geom;   // [4][N]
     float2* d_trig;         // [K] (cos, sin) for the direct comparator
-    int* d_readers;         // per sinogram row k: the linogram rows whose resampling reads
-                            // it, CSR: [K + 1] offsets, then entries 4 (q N + i) + slot
-                            // (0: as row k0, 1: as row k0 + 1, 2: as row 0 mirrored)
+    int* d_readers;         // transposed-resampling table, per group of kRsRows sinogram
+                            // rows: [groups + 1] CSR offsets into d_reader_ent
+    fbp::ReaderEntry* d_reader_ent;
     int* d_status;          // device status word
     // workspace
     void* ws;

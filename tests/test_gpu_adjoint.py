@@ -72,8 +72,9 @@ def test_backprojection_adjoint_integer_inputs_exact(fbp, torch):
                                                                  brute=True))
 
 
-@pytest.mark.parametrize("N", [16, 64])
+@pytest.mark.parametrize("N", [2, 8, 16, 64])
 def test_resampling_adjoint_matches_oracle(fbp, torch, N):
+    # N = 2: K = 3, a partial last group of sinogram rows and the mirrored row-0 reads
     rng = np.random.default_rng(N + 1)
     K, M = phantoms.geometry_for(N)
     lb = rng.normal(size=(1, 4, N, 2 * N)).astype(np.float32)
