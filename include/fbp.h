@@ -169,6 +169,30 @@ fbp_status fbp_resample_st_adjoint(fbp_plan_t plan, const float* d_lin_grad,
 fbp_status fbp_reconstruct_adjoint(fbp_plan_t plan, const float* d_img_grad,
                                    float* d_sino_grad, void* stream);
 
+/* ------------------------------------------------------------------ algebraic reconstruction
+ * The iterative method the paper points to beside its fast FBP (Sec. 4.4: an algebraic
+ * reconstruction built on the fast Hough transform), in its simultaneous form (SIRT) on the
+ * same operators: A = fbp_hough_project (dyadic line sums of an image), A^T =
+ * fbp_fht_backproject (back projection of a linogram).
+ *
+ * fbp_hough_data: sinograms d_sino [batch][K][M] -> Hough-space data d_lin [batch][4][N][2N]
+ * (every entry written): the sinogram sampled bilinearly at the linogram points (Eq. 14-15,
+ * the resampling's positions and angle interpolation, zero outside the detector) divided by
+ * the path length per row sqrt(1 + sigma^2), since a dyadic line visits one pixel per row;
+ * no filter and no row weights.  For an image f, A f approximates fbp_hough_data of its
+ * sinogram.
+ *
+ * fbp_sirt: `iters` steps of f <- f + lambda C^-1 A^T (R^-1 (b - A f)), R = A 1 (pixels on
+ * each line), C = A^T 1 (lines through each pixel), entries where R or C vanishes left out,
+ * on images d_img [batch][N][N] (in: the starting image, e.g. zeros or the fast FBP; out:
+ * the result) for data d_lin_data [batch][4][N][2N].  0 < lambda < 2 (else
+ * FBP_ERR_INVALID_ARG); iters >= 0.  Float32.  The first call makes the plan's R^-1 and
+ * C^-1 tables (one slice, 40 N^2 bytes) and uses both workspaces.  Errors as
+ * fbp_reconstruct. */
+fbp_status fbp_hough_data(fbp_plan_t plan, const float* d_sino, float* d_lin, void* stream);
+fbp_status fbp_sirt(fbp_plan_t plan, const float* d_lin_data, float* d_img, int iters,
+                    float lambda, void* stream);
+
 /* ------------------------------------------------------------------ learned corrector
  * A residual CNN applied after the fast reconstruction, y = x + net(x): six 3x3
  * convolutions (1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1 channels, zero padding, ReLU between),

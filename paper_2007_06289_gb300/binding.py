@@ -69,6 +69,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "fbp_direct_reconstruct": (I, [P, V, V, V]),
         "fbp_fht_backproject_adjoint": (I, [P, V, V, V]),
         "fbp_hough_project": (I, [P, V, V, V]),
+        "fbp_hough_data": (I, [P, V, V, V]),
+        "fbp_sirt": (I, [P, V, V, I, F, V]),
         "fbp_resample_st_adjoint": (I, [P, V, V, V]),
         "fbp_reconstruct_adjoint": (I, [P, V, V, V]),
         "fbp_fht_backproject_static": (I, [I, I, V, V, V]),
@@ -285,6 +287,19 @@ def fbp_hough_project(plan: Plan, img, lin, stream=None) -> None:
     _check("fbp_hough_project", load_library().fbp_hough_project(
         plan.handle, _dev_ptr(img, plan.img_shape, "img"),
         _dev_ptr(lin, plan.lin_shape, "lin"), _stream_ptr(stream)))
+
+
+def fbp_hough_data(plan: Plan, sino, lin, stream=None) -> None:
+    _check("fbp_hough_data", load_library().fbp_hough_data(
+        plan.handle, _dev_ptr(sino, plan.sino_shape, "sino"),
+        _dev_ptr(lin, plan.lin_shape, "lin"), _stream_ptr(stream)))
+
+
+def fbp_sirt(plan: Plan, lin_data, img, iters: int, lam: float = 1.0, stream=None) -> None:
+    """`iters` SIRT steps on img (in/out) for Hough-space data lin_data."""
+    _check("fbp_sirt", load_library().fbp_sirt(
+        plan.handle, _dev_ptr(lin_data, plan.lin_shape, "lin_data"),
+        _dev_ptr(img, plan.img_shape, "img"), int(iters), float(lam), _stream_ptr(stream)))
 
 
 def fbp_resample_st_adjoint(plan: Plan, lin_grad, filt_grad, stream=None) -> None:

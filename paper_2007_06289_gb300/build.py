@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libfbp.so")
-SOURCES = ("fbp_api.cu", "iir_ramp.cu", "fht.cu", "direct.cu", "noalloc.cu", "volume.cu", "adjoint.cu", "cnn.cu")
+SOURCES = ("fbp_api.cu", "iir_ramp.cu", "fht.cu", "direct.cu", "noalloc.cu", "volume.cu", "adjoint.cu", "cnn.cu", "sirt.cu")
 ARCH = ("-gencode", "arch=compute_103a,code=sm_103a")
 FLAGS = ("-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
          "--expt-relaxed-constexpr")

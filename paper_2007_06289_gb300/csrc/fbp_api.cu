@@ -261,9 +261,11 @@ long long to_fixed(double v) { return llround(ldexp(v, fbp::kFixBits)); }
 // atan(sigma), pi - atan(sigma), pi/2 - atan(sigma), pi/2 + atan(sigma).  For stored
 // column c (intercept u = c, or N-1-c for the '+' quarters) the signed offset from the
 // centre c0 is r = (c - c0 (1 + sigma)) / sqrt(1 + sigma^2), negated for h+.
-std::vector<fbp::RowGeom> build_geometry(int N, int K, int M)
+std::vector<fbp::RowGeom> build_geometry(int N, int K, int M,
+                                         std::vector<float2>* hough_w = nullptr)
 {
     std::vector<fbp::RowGeom> g(4 * (size_t)N);
+    if (hough_w) hough_w->assign(4 * (size_t)N, make_float2(0.0f, 0.0f));
     const double c0 = 0.5 * (N - 1);
     const double half = 0.5 * (M - 1);
     for (int q = 0; q < 4; ++q) {
@@ -289,6 +291,8 @@ std::vector<fbp::RowGeom> build_geometry(int N, int K, int M)
             e.w0 = (float)(w * (1.0 - ft));
             e.w1 = (float)(w * ft);
             const double inv = 1.0 / sqrt(1.0 + s * s);
+            if (hough_w)        // angle weights over the path length per row, no w
+                (*hough_w)[(size_t)q * N + i] = make_float2((float)((1.0 - ft) * inv), (float)(ft * inv));
             double A = inv, B = -c0 * (1.0 + s) * inv;
             if (q == 3) { A = -A; B = -B; }
             e.a_fx = to_fixed(A);
@@ -575,7 +579,8 @@ fbp_status fbp_plan(fbp_plan_t* out, int N, int K, int M, int batch,
     layout_workspace(p, default_chunk(p));
 
     fbp_status st = FBP_OK;
-    std::vector<fbp::RowGeom> geo = build_geometry(N, K, M);
+    std::vector<float2> hough_w;
+    std::vector<fbp::RowGeom> geo = build_geometry(N, K, M, &hough_w);
     std::vector<float2> trig(K);
     for (int k = 0; k < K; ++k) {
         const double th = k * M_PI / K;
@@ -587,6 +592,7 @@ fbp_status fbp_plan(fbp_plan_t* out, int N, int K, int M, int batch,
     if (e == cudaSuccess) e = cudaMalloc(&p->d_readers, readers.ptr.size() * sizeof(int));
     if (e == cudaSuccess)
         e = cudaMalloc(&p->d_reader_ent, readers.ent.size() * sizeof(fbp::ReaderEntry));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_hough_w, hough_w.size() * sizeof(float2));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
     if (e != cudaSuccess) st = FBP_ERR_OOM;
     if (st == FBP_OK) {
@@ -598,6 +604,9 @@ fbp_status fbp_plan(fbp_plan_t* out, int N, int K, int M, int batch,
         if (e == cudaSuccess)
             e = cudaMemcpy(p->d_reader_ent, readers.ent.data(),
                            readers.ent.size() * sizeof(fbp::ReaderEntry), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_hough_w, hough_w.data(), hough_w.size() * sizeof(float2),
+                           cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
         if (e == cudaSuccess) e = fbp::prepare_fht_kernels();
         if (e == cudaSuccess) e = fbp::prepare_iir_kernels();
@@ -636,6 +645,8 @@ fbp_status fbp_plan_destroy(fbp_plan_t p)
     if (p->d_trig) cudaFree(p->d_trig);
     if (p->d_readers) cudaFree(p->d_readers);
     if (p->d_reader_ent) cudaFree(p->d_reader_ent);
+    if (p->d_hough_w) cudaFree(p->d_hough_w);
+    if (p->d_sirt) cudaFree(p->d_sirt);
     if (p->d_status) cudaFree(p->d_status);
     cudaStream_t ss[3] = {p->st_h2d, p->st_comp, p->st_d2h};
     for (cudaStream_t s : ss)
@@ -727,6 +738,29 @@ fbp_status fbp_resample_st(fbp_plan_t p, const float* d_filt, float* d_lin, void
     return FBP_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Back projection of cnt linograms (pass 1 from the linogram, pass 2 with the quarter sum)
+// through the workspace's first-pass buffer.
+cudaError_t backproject_lin_chunk(fbp_plan_s* p, const float* lin, float* img, int cnt,
+                                  cudaStream_t st)
+{
+    float* gbuf = ws_ptr(p, p->off_g);
+    cudaError_t e = run(p, FBP_KERNEL_PASS1_LINOGRAM, st,
+                        [&] { return fbp::launch_pass1(p, lin, true, gbuf, cnt, st); });
+    if (e == cudaSuccess)
+        e = run(p, FBP_KERNEL_PASS2, st, [&] { return fbp::launch_pass2(p, gbuf, img, cnt, false, st); });
+    if (e == cudaSuccess && p->n2 > 0)
+        e = run(p, FBP_KERNEL_PASS2_H, st, [&] { return fbp::launch_pass2(p, gbuf, img, cnt, true, st); });
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
 fbp_status fbp_fht_backproject(fbp_plan_t p, const float* d_lin, float* d_img, void* stream)
 {
     if (!p || !d_lin || !d_img) return FBP_ERR_INVALID_ARG;
@@ -736,17 +770,10 @@ fbp_status fbp_fht_backproject(fbp_plan_t p, const float* d_lin, float* d_img, v
     fbp_status s = ensure_workspace(p);
     if (s != FBP_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    float* gbuf = ws_ptr(p, p->off_g);
     for (int c = 0; c < p->batch; c += p->chunk) {
         const int cnt = p->batch - c < p->chunk ? p->batch - c : p->chunk;
-        cudaError_t e = run(p, FBP_KERNEL_PASS1_LINOGRAM, st, [&] {
-            return fbp::launch_pass1(p, d_lin + (size_t)c * fbp::lin_floats(p), true, gbuf, cnt, st);
-        });
-        float* img = d_img + (size_t)c * fbp::img_floats(p);
-        if (e == cudaSuccess)
-            e = run(p, FBP_KERNEL_PASS2, st, [&] { return fbp::launch_pass2(p, gbuf, img, cnt, false, st); });
-        if (e == cudaSuccess && p->n2 > 0)
-            e = run(p, FBP_KERNEL_PASS2_H, st, [&] { return fbp::launch_pass2(p, gbuf, img, cnt, true, st); });
+        const cudaError_t e = backproject_lin_chunk(p, d_lin + (size_t)c * fbp::lin_floats(p),
+                                                    d_img + (size_t)c * fbp::img_floats(p), cnt, st);
         if (e != cudaSuccess) return FBP_ERR_CUDA;
     }
     return FBP_OK;
@@ -909,6 +936,89 @@ fbp_status fbp_reconstruct_adjoint(fbp_plan_t p, const float* d_img_grad, float*
             e = fbp::launch_iir(p, pbar, d_sino_grad + (size_t)c * fbp::sino_floats(p),
                                 cnt * p->K, p->M, st);
         if (e != cudaSuccess) return FBP_ERR_CUDA;
+    }
+    return FBP_OK;
+}
+
+// ------------------------------------------------------------------ algebraic reconstruction
+fbp_status fbp_hough_data(fbp_plan_t p, const float* d_sino, float* d_lin, void* stream)
+{
+    if (!p || !d_sino || !d_lin) return FBP_ERR_INVALID_ARG;
+    if (!aligned16(d_sino) || !aligned16(d_lin)) return FBP_ERR_MISALIGNED;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    for (int c = 0; c < p->batch; c += p->chunk) {      // grid z is the chunk's slice count
+        const int cnt = p->batch - c < p->chunk ? p->batch - c : p->chunk;
+        const cudaError_t e = fbp::launch_hough_data(p, d_sino + (size_t)c * fbp::sino_floats(p),
+                                                     d_lin + (size_t)c * fbp::lin_floats(p), cnt,
+                                                     (cudaStream_t)stream);
+        if (e != cudaSuccess) return FBP_ERR_CUDA;
+    }
+    return FBP_OK;
+}
+
+namespace {
+
+// R^-1 = 1 / (A 1) and C^-1 = 1 / (A^T 1) of one slice (0 where those vanish), made once per
+// plan on `st` with the operators themselves.
+fbp_status ensure_sirt_tables(fbp_plan_s* p, cudaStream_t st)
+{
+    if (p->d_sirt) return FBP_OK;
+    const size_t lf = fbp::lin_floats(p), imf = fbp::img_floats(p);
+    float* t = nullptr;
+    if (cudaMalloc(&t, (lf + imf) * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return FBP_ERR_OOM;
+    }
+    float* ones_img = ws_ptr(p, p->off_stage_img[0]);
+    float* ones_lin = adj_lin(p, 0);
+    cudaError_t e = fbp::launch_fill(ones_img, 1.0f, imf, st);
+    if (e == cudaSuccess) e = fbp::launch_fht_adjoint(p, ones_img, t, adj_lin(p, 1), 1, st);
+    if (e == cudaSuccess) e = fbp::launch_recip(t, lf, st);
+    if (e == cudaSuccess) e = fbp::launch_fill(ones_lin, 1.0f, lf, st);
+    if (e == cudaSuccess) e = backproject_lin_chunk(p, ones_lin, t + lf, 1, st);
+    if (e == cudaSuccess) e = fbp::launch_recip(t + lf, imf, st);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        cudaFree(t);
+        return FBP_ERR_CUDA;
+    }
+    p->d_sirt = t;
+    return FBP_OK;
+}
+
+}  // namespace
+
+fbp_status fbp_sirt(fbp_plan_t p, const float* d_lin_data, float* d_img, int iters, float lambda,
+                    void* stream)
+{
+    if (!p || !d_lin_data || !d_img || iters < 0) return FBP_ERR_INVALID_ARG;
+    if (!(lambda > 0.0f && lambda < 2.0f)) return FBP_ERR_INVALID_ARG;
+    if (!aligned16(d_lin_data) || !aligned16(d_img)) return FBP_ERR_MISALIGNED;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    fbp_status s = ensure_workspace(p);
+    if (s == FBP_OK) s = ensure_adjoint_workspace(p);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s == FBP_OK) s = ensure_sirt_tables(p, st);
+    if (s != FBP_OK) return s;
+    const size_t lf = fbp::lin_floats(p), imf = fbp::img_floats(p);
+    const float* rinv = p->d_sirt;
+    const float* cinv = p->d_sirt + lf;
+    float* ax = adj_lin(p, 0);
+    float* scratch = adj_lin(p, 1);
+    float* atr = ws_ptr(p, p->off_stage_img[0]);
+    for (int c = 0; c < p->batch; c += p->chunk) {
+        const int cnt = p->batch - c < p->chunk ? p->batch - c : p->chunk;
+        const float* b = d_lin_data + (size_t)c * lf;
+        float* f = d_img + (size_t)c * imf;
+        for (int it = 0; it < iters; ++it) {
+            cudaError_t e = fbp::launch_fht_adjoint(p, f, ax, scratch, cnt, st);       // A f
+            if (e == cudaSuccess) e = fbp::launch_sirt_residual(b, ax, rinv, lf, cnt, st);
+            if (e == cudaSuccess) e = backproject_lin_chunk(p, ax, atr, cnt, st);     // A^T r
+            if (e == cudaSuccess) e = fbp::launch_sirt_update(f, atr, cinv, lambda, imf, cnt, st);
+            if (e != cudaSuccess) return FBP_ERR_CUDA;
+        }
     }
     return FBP_OK;
 }

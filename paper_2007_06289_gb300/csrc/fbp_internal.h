@@ -80,6 +80,9 @@ struct fbp_plan_s {
     int* d_readers;         // transposed-resampling table, per group of kRsRows sinogram
                             // rows: [groups + 1] CSR offsets into d_reader_ent
     fbp::ReaderEntry* d_reader_ent;
+    float2* d_hough_w;      // [4][N]: ((1 - ft), ft) / sqrt(1 + sigma^2), Hough-space data
+    float* d_sirt;          // SIRT tables of one slice, made on first use: R^-1 [4][N][2N],
+                            // then C^-1 [N][N]
     int* d_status;          // device status word
     // workspace
     void* ws;
@@ -130,6 +133,18 @@ cudaError_t launch_resample_adjoint(const fbp_plan_s* p, const float* lin_grad, 
                                     int count, cudaStream_t st);
 cudaError_t launch_direct_bp(const fbp_plan_s* p, const float* filt, float* img, int count,
                              cudaStream_t st);
+// Algebraic reconstruction (sirt.cu): Hough-space data of a sinogram [count][K][M] ->
+// [count][4][N][2N]; r = (b - r) * rinv and f = f + lam * cinv * t elementwise, rinv / cinv
+// one slice's [per_slice] array shared by all count slices (per_slice a multiple of 4);
+// fill and reciprocal (0 where not positive).
+cudaError_t launch_hough_data(const fbp_plan_s* p, const float* sino, float* lin, int count,
+                              cudaStream_t st);
+cudaError_t launch_sirt_residual(const float* b, float* r, const float* rinv, size_t per_slice,
+                                 int count, cudaStream_t st);
+cudaError_t launch_sirt_update(float* f, const float* t, const float* cinv, float lam,
+                               size_t per_slice, int count, cudaStream_t st);
+cudaError_t launch_fill(float* x, float v, size_t n, cudaStream_t st);
+cudaError_t launch_recip(float* x, size_t n, cudaStream_t st);
 
 // The fused pipeline keeps its filtered sinogram with kGuard zero bins on both sides of
 // every row, so resampling reads bins -kGuard .. M+kGuard-1 without range checks.

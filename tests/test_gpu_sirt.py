@@ -1,0 +1,102 @@
+"""Algebraic reconstruction (SIRT on the fast Hough operators) on the GPU against the oracle.
+
+Tolerances: the Hough-space data use the resampling's float32 positions and weights
+(compared at 1e-6 of the largest value); SIRT iterates float32 sums of the exact operators,
+compared with the float64 oracle after a few steps at 1e-5 of the largest pixel.
+"""
+import numpy as np
+import pytest
+
+import oracle.sirt as so
+import phantoms
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need CUDA"
+    return t
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+@pytest.mark.parametrize("N", [2, 16, 64])
+def test_hough_data_matches_oracle(fbp, torch, N):
+    K, M = phantoms.geometry_for(N)
+    rng = np.random.default_rng(N)
+    sino = rng.normal(size=(2, K, M)).astype(np.float32)
+    plan = fbp.fbp_plan(N, K, M, 2)
+    lin = torch.full(plan.lin_shape, float("nan"), device="cuda")
+    fbp.fbp_hough_data(plan, dev(torch, sino), lin)
+    torch.cuda.synchronize()
+    got = lin.cpu().numpy()
+    for s in range(2):
+        want = so.hough_data(sino[s].astype(np.float64), N)
+        assert np.abs(got[s] - want).max() <= 1e-6 * np.abs(want).max()
+
+
+def test_sirt_matches_oracle(fbp, torch):
+    N, B, iters = 32, 2, 5
+    K, M = phantoms.geometry_for(N)
+    rng = np.random.default_rng(3)
+    f_true = rng.normal(size=(B, N, N))
+    b = np.stack([so.hough_project(f_true[s]) for s in range(B)]).astype(np.float32)
+    b = b + (0.05 * rng.normal(size=b.shape) * (b != 0)).astype(np.float32)
+    plan = fbp.fbp_plan(N, K, M, B)
+    img = torch.zeros(plan.img_shape, device="cuda")
+    fbp.fbp_sirt(plan, dev(torch, b), img, iters, 1.2)
+    torch.cuda.synchronize()
+    got = img.cpu().numpy()
+    for s in range(B):
+        want = so.sirt(b[s].astype(np.float64), N, iters, 1.2)
+        assert np.abs(got[s] - want).max() <= 1e-5 * np.abs(want).max()
+
+
+def test_sirt_recovers_the_image_from_consistent_data(fbp, torch):
+    # data from the GPU projector of a phantom image; the error falls with the iterations
+    N = 64
+    K, M = phantoms.geometry_for(N)
+    plan = fbp.fbp_plan(N, K, M, 1)
+    gen = torch.Generator(device="cuda").manual_seed(4)
+    f_true = torch.rand(plan.img_shape, device="cuda", generator=gen)
+    b = torch.empty(plan.lin_shape, device="cuda")
+    fbp.fbp_hough_project(plan, f_true, b)
+    img = torch.zeros(plan.img_shape, device="cuda")
+    errs = []
+    for _ in range(4):
+        fbp.fbp_sirt(plan, b, img, 50, 1.5)
+        errs.append(float(torch.linalg.norm(img - f_true) / torch.linalg.norm(f_true)))
+    assert all(e1 < e0 for e0, e1 in zip(errs, errs[1:])), errs
+    assert errs[-1] < 0.5 * errs[0], errs
+
+
+def test_sirt_chunks_equal_single_slices(fbp, torch):
+    N, B = 32, 3
+    K, M = phantoms.geometry_for(N)
+    rng = np.random.default_rng(5)
+    b = dev(torch, np.stack([so.hough_project(rng.normal(size=(N, N))) for _ in range(B)]))
+    plan = fbp.fbp_plan(N, K, M, B)
+    fbp.fbp_set_chunk(plan, 2)
+    img = torch.zeros(plan.img_shape, device="cuda")
+    fbp.fbp_sirt(plan, b, img, 3, 1.0)
+    one = fbp.fbp_plan(N, K, M, 1)
+    for s in range(B):
+        ref = torch.zeros(one.img_shape, device="cuda")
+        fbp.fbp_sirt(one, b[s:s + 1].contiguous(), ref, 3, 1.0)
+        torch.cuda.synchronize()
+        assert torch.equal(img[s:s + 1], ref)
+
+
+def test_sirt_rejects_bad_relaxation(fbp, torch):
+    N = 8
+    K, M = phantoms.geometry_for(N)
+    plan = fbp.fbp_plan(N, K, M, 1)
+    b = torch.zeros(plan.lin_shape, device="cuda")
+    img = torch.zeros(plan.img_shape, device="cuda")
+    for lam in (0.0, 2.0, -1.0, float("nan")):
+        with pytest.raises(RuntimeError):
+            fbp.fbp_sirt(plan, b, img, 1, lam)

@@ -33,6 +33,11 @@ MISTAKES = [
      "xp[:, 2 - dy:2 - dy + H, 2 - dx:2 - dx + W])\n    return out"),         # convolution, not correlation
     ("cnn.py", "gh = gin * (hin > 0.0)", "gh = gin"),                          # ReLU mask dropped
     ("cnn.py", "return x + h[0], cache", "return h[0], cache"),                 # no skip connection
+    # algebraic reconstruction
+    ("sirt.py", "f = f + lam * cinv * back_project(", "f = f + lam * back_project("),  # no C^-1
+    ("sirt.py", "(b - hough_project(f))", "(hough_project(f) - b)"),             # residual sign
+    ("sirt.py", "scale = 1.0 / (row_weights(N) * np.sqrt(1.0 + sigma * sigma))",
+     "scale = 1.0 / row_weights(N)"),                                         # no path length
 ]
 
 
@@ -50,6 +55,6 @@ def test_planted_mistake_is_caught(tmp_path, fname, old, new):
                         "tests/test_oracle_iir.py", "tests/test_oracle_geometry.py",
                         "tests/test_oracle_linogram.py", "tests/test_oracle_dyadic.py",
                         "tests/test_oracle_fbp.py", "tests/test_oracle_adjoint.py",
-                        "tests/test_oracle_cnn.py"],
+                        "tests/test_oracle_cnn.py", "tests/test_oracle_sirt.py"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, r.stdout[-2000:]
