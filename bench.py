@@ -799,7 +799,9 @@ def run_sirt(args):
     fbp.fbp_sirt(plan, data, img, 40, LAM)
     q["rmse_sirt_50_from_fbp"] = rmse(img)
     n = N.bit_length() - 1
-    per_iter = -(-n // 5) + 1 + 2 + (1 if plan.fuse_k < n else 0) + 1
+    # per chunk and iteration: the fused projection launches (the last one forms the
+    # residual), the two or three back-projection passes, the update
+    per_iter = -(-n // 5) + 2 + (1 if plan.fuse_k < n else 0) + 1
     line = {"metric": "slice-iterations/s of SIRT on the fast Hough operators at N=512, batch 16",
             "value": round(B * IT * world / (ms / 1e3), 1), "unit": "slice-iterations/s",
             "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),

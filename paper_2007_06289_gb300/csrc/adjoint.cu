@@ -53,10 +53,12 @@ template <int S> constexpr int af_tile() { return kAfCols - af_halo<S>(); }
 constexpr int kAfPitch = kAfCols + 1;           // odd: conflict-free column-wise writes
 template <int S> constexpr size_t af_smem() { return 2 * (size_t)(1 << S) * kAfPitch * sizeof(float); }
 
-template <int S, bool FROM_IMAGE>
+// RESID (last launch only): the output is turned into the SIRT residual on the way out,
+// (b - out) * rinv, b [count][4][N][2N] and rinv one slice's [4][N][2N].
+template <int S, bool FROM_IMAGE, bool RESID>
 __global__ void __launch_bounds__(kAdjThreads)
 adj_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int N, int n, int k,
-                 int wc)
+                 int wc, const float* __restrict__ rb, const float* __restrict__ rw)
 {
     constexpr int R = 1 << S;
     constexpr int H = af_halo<S>();
@@ -122,6 +124,20 @@ adj_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int N, i
 #pragma unroll
         for (int j = 0; j < R; ++j) X[j * kAfPitch + tid] = v[j];
     }
+    // RESID: the last launch (t = 0, so output row C lands at column x itself); start this
+    // thread's data and weight loads now so that they arrive during the stage sweeps
+    float rbv[RESID ? R : 1], rwv[RESID ? R : 1];
+    if constexpr (RESID) {
+        const int x = xs + tid;
+        const bool ok = tid >= H && x < xa + wc && x < W;
+        const size_t o = ((size_t)sq * N + ((size_t)b << S)) * W + x;
+        const size_t ow = o - (size_t)(sq >> 2) * 4 * N * W;
+#pragma unroll
+        for (int C = 0; C < R; ++C) {
+            rbv[C] = ok ? rb[o + (size_t)C * W] : 0.0f;
+            rwv[C] = ok ? rw[ow + (size_t)C * W] : 0.0f;
+        }
+    }
     __syncthreads();
 
     // S transposed stages on the 2^S rows (slopes of the group alone), ping-ponging between
@@ -159,11 +175,16 @@ adj_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int N, i
     if (p >= H) {
         const int x = xs + p;
         if (x < xa + wc) {
-            float* orow = out + ((size_t)sq * N + ((size_t)b << (S + ko)) + t) * W + x;
+            const size_t o = ((size_t)sq * N + ((size_t)b << (S + ko)) + t) * W + x;
 #pragma unroll
             for (int C = 0; C < R; ++C) {
                 const int v = x + C * t;
-                if (v < W) orow[((size_t)C << ko) * W + (size_t)C * t] = cur[C * kAfPitch + p];
+                if (v < W) {
+                    const size_t oc = o + ((size_t)C << ko) * W + (size_t)C * t;
+                    float val = cur[C * kAfPitch + p];
+                    if constexpr (RESID) val = (rbv[C] - val) * rwv[C];
+                    out[oc] = val;
+                }
             }
         }
     }
@@ -172,26 +193,33 @@ adj_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int N, i
 template <int S>
 cudaError_t set_af_attr()
 {
-    cudaError_t e = cudaFuncSetAttribute(adj_fused_kernel<S, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)af_smem<S>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(adj_fused_kernel<S, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)af_smem<S>());
+    const int bytes = (int)af_smem<S>();
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(adj_fused_kernel<S, true, false>, a, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(adj_fused_kernel<S, false, false>, a, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(adj_fused_kernel<S, true, true>, a, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(adj_fused_kernel<S, false, true>, a, bytes);
     return e;
 }
 
 template <int S>
 cudaError_t launch_af(const float* in, float* out, int N, int n, int k, int count, bool from_image,
-                      cudaStream_t st)
+                      const float* rb, const float* rw, cudaStream_t st)
 {
     const int W = 2 * N;
     // written length of every output row: the last launch (level 0) writes all W columns
     const int wc = k == S ? W : N + (1 << (n - k + S)) - 1;
     const dim3 grid((wc + af_tile<S>() - 1) / af_tile<S>(), N >> S, 4 * count);
-    if (from_image)
-        adj_fused_kernel<S, true><<<grid, kAdjThreads, af_smem<S>(), st>>>(in, out, N, n, k, wc);
+    const size_t sm = af_smem<S>();
+    const bool resid = rb != nullptr && k == S;
+    if (from_image && resid)
+        adj_fused_kernel<S, true, true><<<grid, kAdjThreads, sm, st>>>(in, out, N, n, k, wc, rb, rw);
+    else if (from_image)
+        adj_fused_kernel<S, true, false><<<grid, kAdjThreads, sm, st>>>(in, out, N, n, k, wc, rb, rw);
+    else if (resid)
+        adj_fused_kernel<S, false, true><<<grid, kAdjThreads, sm, st>>>(in, out, N, n, k, wc, rb, rw);
     else
-        adj_fused_kernel<S, false><<<grid, kAdjThreads, af_smem<S>(), st>>>(in, out, N, n, k, wc);
+        adj_fused_kernel<S, false, false><<<grid, kAdjThreads, sm, st>>>(in, out, N, n, k, wc, rb, rw);
     return cudaGetLastError();
 }
 
@@ -321,7 +349,8 @@ cudaError_t prepare_adjoint_kernels()
 }
 
 cudaError_t launch_fht_adjoint(const fbp_plan_s* p, const float* img_grad, float* lin_grad,
-                               float* scratch, int count, cudaStream_t st)
+                               float* scratch, int count, cudaStream_t st, const float* resid_b,
+                               const float* resid_w)
 {
     if (count <= 0) return cudaSuccess;
     const int N = p->N, n = p->n;
@@ -337,11 +366,11 @@ cudaError_t launch_fht_adjoint(const fbp_plan_s* p, const float* img_grad, float
         const int left = launches - l;
         const int S = (k + left - 1) / left;
         switch (S) {
-            case 1: e = launch_af<1>(src, buf[cur], N, n, k, count, l == 0, st); break;
-            case 2: e = launch_af<2>(src, buf[cur], N, n, k, count, l == 0, st); break;
-            case 3: e = launch_af<3>(src, buf[cur], N, n, k, count, l == 0, st); break;
-            case 4: e = launch_af<4>(src, buf[cur], N, n, k, count, l == 0, st); break;
-            default: e = launch_af<5>(src, buf[cur], N, n, k, count, l == 0, st); break;
+            case 1: e = launch_af<1>(src, buf[cur], N, n, k, count, l == 0, resid_b, resid_w, st); break;
+            case 2: e = launch_af<2>(src, buf[cur], N, n, k, count, l == 0, resid_b, resid_w, st); break;
+            case 3: e = launch_af<3>(src, buf[cur], N, n, k, count, l == 0, resid_b, resid_w, st); break;
+            case 4: e = launch_af<4>(src, buf[cur], N, n, k, count, l == 0, resid_b, resid_w, st); break;
+            default: e = launch_af<5>(src, buf[cur], N, n, k, count, l == 0, resid_b, resid_w, st); break;
         }
         src = buf[cur];
         cur ^= 1;

@@ -1013,8 +1013,8 @@ fbp_status fbp_sirt(fbp_plan_t p, const float* d_lin_data, float* d_img, int ite
         const float* b = d_lin_data + (size_t)c * lf;
         float* f = d_img + (size_t)c * imf;
         for (int it = 0; it < iters; ++it) {
-            cudaError_t e = fbp::launch_fht_adjoint(p, f, ax, scratch, cnt, st);       // A f
-            if (e == cudaSuccess) e = fbp::launch_sirt_residual(b, ax, rinv, lf, cnt, st);
+            // r = (b - A f) R^-1, formed as the projection's last launch writes A f
+            cudaError_t e = fbp::launch_fht_adjoint(p, f, ax, scratch, cnt, st, b, rinv);
             if (e == cudaSuccess) e = backproject_lin_chunk(p, ax, atr, cnt, st);     // A^T r
             if (e == cudaSuccess) e = fbp::launch_sirt_update(f, atr, cinv, lambda, imf, cnt, st);
             if (e != cudaSuccess) return FBP_ERR_CUDA;

@@ -127,20 +127,21 @@ cudaError_t launch_fir(const fbp_plan_s* p, const float* in, float* out, int row
 // Adjoints: image gradient [count][N][N] -> linogram gradient [count][4][N][2N] (scratch:
 // another [count][4][N][2N] buffer), and linogram gradient -> filtered-sinogram gradient
 // [count][K][M] (zeroed, then scattered into).
+// resid_b / resid_w (optional): write the SIRT residual (resid_b - A f) * resid_w instead
+// of A f, resid_b [count][4][N][2N], resid_w one slice's [4][N][2N].
 cudaError_t launch_fht_adjoint(const fbp_plan_s* p, const float* img_grad, float* lin_grad,
-                               float* scratch, int count, cudaStream_t st);
+                               float* scratch, int count, cudaStream_t st,
+                               const float* resid_b = nullptr, const float* resid_w = nullptr);
 cudaError_t launch_resample_adjoint(const fbp_plan_s* p, const float* lin_grad, float* filt_grad,
                                     int count, cudaStream_t st);
 cudaError_t launch_direct_bp(const fbp_plan_s* p, const float* filt, float* img, int count,
                              cudaStream_t st);
 // Algebraic reconstruction (sirt.cu): Hough-space data of a sinogram [count][K][M] ->
-// [count][4][N][2N]; r = (b - r) * rinv and f = f + lam * cinv * t elementwise, rinv / cinv
-// one slice's [per_slice] array shared by all count slices (per_slice a multiple of 4);
-// fill and reciprocal (0 where not positive).
+// [count][4][N][2N]; f = f + lam * cinv * t elementwise, cinv one slice's [per_slice] array
+// shared by all count slices (per_slice a multiple of 4); fill and reciprocal (0 where not
+// positive).
 cudaError_t launch_hough_data(const fbp_plan_s* p, const float* sino, float* lin, int count,
                               cudaStream_t st);
-cudaError_t launch_sirt_residual(const float* b, float* r, const float* rinv, size_t per_slice,
-                                 int count, cudaStream_t st);
 cudaError_t launch_sirt_update(float* f, const float* t, const float* cinv, float lam,
                                size_t per_slice, int count, cudaStream_t st);
 cudaError_t launch_fill(float* x, float v, size_t n, cudaStream_t st);

@@ -2,10 +2,12 @@
 // paper points to in Sec. 4.4), in its simultaneous form:
 //     f <- f + lam C^-1 A^T (R^-1 (b - A f)),   R = A 1,  C = A^T 1,
 // A the dyadic line sums of an image (the transposed back projection, adjoint.cu) and A^T
-// the back projection of a linogram (the two Hough passes, fht.cu).  This file holds the
-// elementwise steps around those operators and the conversion of a sinogram into Hough-space
-// data (the sinogram sampled at the linogram points, Eq. 14-15, divided by the path length
-// per row sqrt(1 + sigma^2), since a dyadic line visits one pixel per row).
+// the back projection of a linogram (the two Hough passes, fht.cu).  The residual
+// (b - A f) R^-1 is formed by the projection's last launch as it writes A f (adjoint.cu).
+// This file holds the update step, the fill and reciprocal that make R^-1 and C^-1, and the
+// conversion of a sinogram into Hough-space data (the sinogram sampled at the linogram
+// points, Eq. 14-15, divided by the path length per row sqrt(1 + sigma^2), since a dyadic
+// line visits one pixel per row).
 #include "fbp_internal.h"
 
 namespace fbp {
@@ -55,19 +57,6 @@ hough_data_kernel(const float* __restrict__ sino, float* __restrict__ lin,
     lin[((size_t)s * 4 * N + qi) * W + c] = fmaf(w.y, vb, w.x * va);
 }
 
-// r = (b - r) * rinv, rinv shared by all slices (per_slice floats, a multiple of 4)
-__global__ void __launch_bounds__(kSirtThreads)
-sirt_residual_kernel(const float4* __restrict__ b, float4* __restrict__ r,
-                     const float4* __restrict__ rinv, size_t per_slice4, size_t total4)
-{
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total4;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const float4 bb = b[i], rr = r[i], w = rinv[i % per_slice4];
-        r[i] = make_float4((bb.x - rr.x) * w.x, (bb.y - rr.y) * w.y, (bb.z - rr.z) * w.z,
-                           (bb.w - rr.w) * w.w);
-    }
-}
-
 // f = f + lam * cinv * t
 __global__ void __launch_bounds__(kSirtThreads)
 sirt_update_kernel(float4* __restrict__ f, const float4* __restrict__ t,
@@ -113,16 +102,6 @@ cudaError_t launch_hough_data(const fbp_plan_s* p, const float* sino, float* lin
     const dim3 grid((2 * p->N + kSirtThreads - 1) / kSirtThreads, 4 * p->N, count);
     hough_data_kernel<<<grid, kSirtThreads, 0, st>>>(sino, lin, p->d_geom, p->d_hough_w, p->N,
                                                      p->K, p->M);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_sirt_residual(const float* b, float* r, const float* rinv, size_t per_slice,
-                                 int count, cudaStream_t st)
-{
-    const size_t total4 = per_slice / 4 * count;
-    sirt_residual_kernel<<<stream_grid(total4), kSirtThreads, 0, st>>>(
-        reinterpret_cast<const float4*>(b), reinterpret_cast<float4*>(r),
-        reinterpret_cast<const float4*>(rinv), per_slice / 4, total4);
     return cudaGetLastError();
 }
 
