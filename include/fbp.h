@@ -190,6 +190,14 @@ fbp_status fbp_reconstruct_adjoint(fbp_plan_t plan, const float* d_img_grad,
  * C^-1 tables (one slice, 40 N^2 bytes) and uses both workspaces.  Errors as
  * fbp_reconstruct. */
 fbp_status fbp_hough_data(fbp_plan_t plan, const float* d_sino, float* d_lin, void* stream);
+
+/* Fast (approximate) Radon transform: images d_img [batch][N][N] -> sinograms d_sino
+ * [batch][K][M] (every entry written), theta_k = k pi / K, r_m = m - (M-1)/2.  The dyadic
+ * line sums of fbp_hough_project (Eq. 17) resampled: for each theta_k its line class and
+ * slope sigma, the two linogram rows around sigma (N-1) read at the column of offset r_m
+ * (linear in the column), mixed linearly in the slope, times the path length per row
+ * sqrt(1 + sigma^2).  Uses the adjoint workspace.  Errors as fbp_reconstruct. */
+fbp_status fbp_radon(fbp_plan_t plan, const float* d_img, float* d_sino, void* stream);
 fbp_status fbp_sirt(fbp_plan_t plan, const float* d_lin_data, float* d_img, int iters,
                     float lambda, void* stream);
 

@@ -70,6 +70,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "fbp_fht_backproject_adjoint": (I, [P, V, V, V]),
         "fbp_hough_project": (I, [P, V, V, V]),
         "fbp_hough_data": (I, [P, V, V, V]),
+        "fbp_radon": (I, [P, V, V, V]),
         "fbp_sirt": (I, [P, V, V, I, F, V]),
         "fbp_resample_st_adjoint": (I, [P, V, V, V]),
         "fbp_reconstruct_adjoint": (I, [P, V, V, V]),
@@ -293,6 +294,12 @@ def fbp_hough_data(plan: Plan, sino, lin, stream=None) -> None:
     _check("fbp_hough_data", load_library().fbp_hough_data(
         plan.handle, _dev_ptr(sino, plan.sino_shape, "sino"),
         _dev_ptr(lin, plan.lin_shape, "lin"), _stream_ptr(stream)))
+
+
+def fbp_radon(plan: Plan, img, sino, stream=None) -> None:
+    _check("fbp_radon", load_library().fbp_radon(
+        plan.handle, _dev_ptr(img, plan.img_shape, "img"),
+        _dev_ptr(sino, plan.sino_shape, "sino"), _stream_ptr(stream)))
 
 
 def fbp_sirt(plan: Plan, lin_data, img, iters: int, lam: float = 1.0, stream=None) -> None:

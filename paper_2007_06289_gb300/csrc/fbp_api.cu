@@ -349,6 +349,62 @@ ReaderTable build_readers(const std::vector<fbp::RowGeom>& geo, int K)
     return t;
 }
 
+// Fast Radon transform table (float64 geometry, then 32.32 fixed point): per sinogram row,
+// the line class holding theta_k (v- up to pi/4, h- up to pi/2, h+ up to 3pi/4, v+ beyond;
+// slope sigma = tan of the angle to the class's axis), the two linogram rows around
+// sigma (N-1), and in each the stored column of detector bin m: the row's offset r is affine
+// in the column, r(c) = r0 + dr c, so c = (m - (M-1)/2 - r0) / dr.
+double class_angle(int q, double s)
+{
+    const double at = atan(s);
+    switch (q) {
+        case 0: return at;
+        case 1: return M_PI - at;
+        case 2: return 0.5 * M_PI - at;
+        default: return 0.5 * M_PI + at;
+    }
+}
+
+double class_offset(int q, double s, double c, int N)     // r of stored column c
+{
+    const double c0 = 0.5 * (N - 1);
+    const double th = class_angle(q, s);
+    const double u = (q == 0 || q == 2) ? c : (N - 1) - c;
+    const double x = q < 2 ? u : 0.0, y = q < 2 ? 0.0 : u;
+    return (x - c0) * cos(th) + (y - c0) * sin(th);
+}
+
+std::vector<fbp::RadonRow> build_radon(int N, int K, int M)
+{
+    std::vector<fbp::RadonRow> t(K);
+    for (int k = 0; k < K; ++k) {
+        const double th = k * M_PI / K;
+        int q;
+        double s;
+        if (th <= M_PI / 4) { q = 0; s = tan(th); }
+        else if (th <= M_PI / 2) { q = 2; s = tan(M_PI / 2 - th); }
+        else if (th <= 3 * M_PI / 4) { q = 3; s = tan(th - M_PI / 2); }
+        else { q = 1; s = tan(M_PI - th); }
+        const double istar = s * (N - 1);
+        int i0 = (int)floor(istar);
+        if (i0 > N - 2) i0 = N - 2;
+        if (i0 < 0) i0 = 0;
+        fbp::RadonRow& e = t[k];
+        e.q = q;
+        e.i0 = i0;
+        e.t = (float)(istar - i0);
+        e.scale = (float)sqrt(1.0 + s * s);
+        for (int j = 0; j < 2; ++j) {
+            const double si = (double)(i0 + j) / (N - 1);
+            const double r0 = class_offset(q, si, 0.0, N);
+            const double dr = class_offset(q, si, 1.0, N) - r0;
+            e.a_fx[j] = to_fixed(1.0 / dr);
+            e.b_fx[j] = to_fixed((-0.5 * (M - 1) - r0) / dr);
+        }
+    }
+    return t;
+}
+
 int ilog2(int v)
 {
     int n = 0;
@@ -593,6 +649,8 @@ fbp_status fbp_plan(fbp_plan_t* out, int N, int K, int M, int batch,
     if (e == cudaSuccess)
         e = cudaMalloc(&p->d_reader_ent, readers.ent.size() * sizeof(fbp::ReaderEntry));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_hough_w, hough_w.size() * sizeof(float2));
+    const std::vector<fbp::RadonRow> radon = build_radon(N, K, M);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_radon, radon.size() * sizeof(fbp::RadonRow));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
     if (e != cudaSuccess) st = FBP_ERR_OOM;
     if (st == FBP_OK) {
@@ -606,6 +664,9 @@ fbp_status fbp_plan(fbp_plan_t* out, int N, int K, int M, int batch,
                            readers.ent.size() * sizeof(fbp::ReaderEntry), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemcpy(p->d_hough_w, hough_w.data(), hough_w.size() * sizeof(float2),
+                           cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->d_radon, radon.data(), radon.size() * sizeof(fbp::RadonRow),
                            cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
         if (e == cudaSuccess) e = fbp::prepare_fht_kernels();
@@ -646,6 +707,7 @@ fbp_status fbp_plan_destroy(fbp_plan_t p)
     if (p->d_readers) cudaFree(p->d_readers);
     if (p->d_reader_ent) cudaFree(p->d_reader_ent);
     if (p->d_hough_w) cudaFree(p->d_hough_w);
+    if (p->d_radon) cudaFree(p->d_radon);
     if (p->d_sirt) cudaFree(p->d_sirt);
     if (p->d_status) cudaFree(p->d_status);
     cudaStream_t ss[3] = {p->st_h2d, p->st_comp, p->st_d2h};
@@ -952,6 +1014,27 @@ fbp_status fbp_hough_data(fbp_plan_t p, const float* d_sino, float* d_lin, void*
         const cudaError_t e = fbp::launch_hough_data(p, d_sino + (size_t)c * fbp::sino_floats(p),
                                                      d_lin + (size_t)c * fbp::lin_floats(p), cnt,
                                                      (cudaStream_t)stream);
+        if (e != cudaSuccess) return FBP_ERR_CUDA;
+    }
+    return FBP_OK;
+}
+
+fbp_status fbp_radon(fbp_plan_t p, const float* d_img, float* d_sino, void* stream)
+{
+    if (!p || !d_img || !d_sino) return FBP_ERR_INVALID_ARG;
+    if (!aligned16(d_img) || !aligned16(d_sino)) return FBP_ERR_MISALIGNED;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    fbp_status s = ensure_adjoint_workspace(p);
+    if (s != FBP_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    float* lin = adj_lin(p, 0);
+    for (int c = 0; c < p->batch; c += p->chunk) {
+        const int cnt = p->batch - c < p->chunk ? p->batch - c : p->chunk;
+        cudaError_t e = fbp::launch_fht_adjoint(p, d_img + (size_t)c * fbp::img_floats(p), lin,
+                                                adj_lin(p, 1), cnt, st);   // line sums, Eq. 17
+        if (e == cudaSuccess)
+            e = fbp::launch_radon(p, lin, d_sino + (size_t)c * fbp::sino_floats(p), cnt, st);
         if (e != cudaSuccess) return FBP_ERR_CUDA;
     }
     return FBP_OK;

@@ -66,6 +66,16 @@ struct ReaderEntry {
     int code;
     float w[kRsRows];
 };
+
+// Fast Radon transform, per sinogram row k: the line class q holding theta_k, the two
+// linogram rows i0, i0 + 1 around its slope with weights (1 - t, t), the path length per
+// row `scale` = sqrt(1 + sigma^2), and per row the stored column of detector bin m,
+// c = a m + b in 32.32 fixed point.
+struct RadonRow {
+    int q, i0;
+    float t, scale;
+    long long a_fx[2], b_fx[2];
+};
 }  // namespace fbp
 
 struct fbp_plan_s {
@@ -81,6 +91,7 @@ struct fbp_plan_s {
                             // rows: [groups + 1] CSR offsets into d_reader_ent
     fbp::ReaderEntry* d_reader_ent;
     float2* d_hough_w;      // [4][N]: ((1 - ft), ft) / sqrt(1 + sigma^2), Hough-space data
+    fbp::RadonRow* d_radon; // [K]: the fast Radon transform's resampling
     float* d_sirt;          // SIRT tables of one slice, made on first use: R^-1 [4][N][2N],
                             // then C^-1 [N][N]
     int* d_status;          // device status word
@@ -145,6 +156,9 @@ cudaError_t launch_hough_data(const fbp_plan_s* p, const float* sino, float* lin
 cudaError_t launch_sirt_update(float* f, const float* t, const float* cinv, float lam,
                                size_t per_slice, int count, cudaStream_t st);
 cudaError_t launch_fill(float* x, float v, size_t n, cudaStream_t st);
+// Fast Radon transform: dyadic line sums [count][4][N][2N] -> sinogram [count][K][M].
+cudaError_t launch_radon(const fbp_plan_s* p, const float* lin, float* sino, int count,
+                         cudaStream_t st);
 cudaError_t launch_recip(float* x, size_t n, cudaStream_t st);
 
 // The fused pipeline keeps its filtered sinogram with kGuard zero bins on both sides of

@@ -4,10 +4,11 @@
 // A the dyadic line sums of an image (the transposed back projection, adjoint.cu) and A^T
 // the back projection of a linogram (the two Hough passes, fht.cu).  The residual
 // (b - A f) R^-1 is formed by the projection's last launch as it writes A f (adjoint.cu).
-// This file holds the update step, the fill and reciprocal that make R^-1 and C^-1, and the
+// This file holds the update step, the fill and reciprocal that make R^-1 and C^-1, the
 // conversion of a sinogram into Hough-space data (the sinogram sampled at the linogram
 // points, Eq. 14-15, divided by the path length per row sqrt(1 + sigma^2), since a dyadic
-// line visits one pixel per row).
+// line visits one pixel per row), and the opposite resampling, which turns the line sums of
+// the fast Hough projection (Eq. 17) into a (theta, r) sinogram: a fast Radon transform.
 #include "fbp_internal.h"
 
 namespace fbp {
@@ -57,6 +58,34 @@ hough_data_kernel(const float* __restrict__ sino, float* __restrict__ lin,
     lin[((size_t)s * 4 * N + qi) * W + c] = fmaf(w.y, vb, w.x * va);
 }
 
+// Fast Radon transform: sinogram row k from the dyadic line sums H of its line class, the
+// two linogram rows around its slope read at the column of detector offset r_m (linear in
+// the column, zero outside [0, 2N)), mixed (1 - t, t), times the path length per row.
+__global__ void __launch_bounds__(kSirtThreads)
+radon_kernel(const float* __restrict__ lin, float* __restrict__ sino,
+             const RadonRow* __restrict__ rows, int N, int K, int M)
+{
+    const int W = 2 * N;
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    const int s = blockIdx.z;
+    if (m >= M) return;
+    const RadonRow e = rows[k];
+    const float* h = lin + (((size_t)s * 4 + e.q) * N + e.i0) * W;
+    float v[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const long long cf = e.b_fx[j] + e.a_fx[j] * (long long)m;
+        const int c = (int)(cf >> kFixBits);
+        const float f = __uint2float_rn((unsigned)cf) * 0x1p-32f;
+        const float* row = h + (size_t)j * W;
+        const float h0 = (c >= 0 && c < W) ? row[c] : 0.0f;
+        const float h1 = (c + 1 >= 0 && c + 1 < W) ? row[c + 1] : 0.0f;
+        v[j] = fmaf(f, h1, (1.0f - f) * h0);
+    }
+    sino[((size_t)s * K + k) * M + m] = fmaf(e.t, v[1], (1.0f - e.t) * v[0]) * e.scale;
+}
+
 // f = f + lam * cinv * t
 __global__ void __launch_bounds__(kSirtThreads)
 sirt_update_kernel(float4* __restrict__ f, const float4* __restrict__ t,
@@ -102,6 +131,15 @@ cudaError_t launch_hough_data(const fbp_plan_s* p, const float* sino, float* lin
     const dim3 grid((2 * p->N + kSirtThreads - 1) / kSirtThreads, 4 * p->N, count);
     hough_data_kernel<<<grid, kSirtThreads, 0, st>>>(sino, lin, p->d_geom, p->d_hough_w, p->N,
                                                      p->K, p->M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_radon(const fbp_plan_s* p, const float* lin, float* sino, int count,
+                         cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    const dim3 grid((p->M + kSirtThreads - 1) / kSirtThreads, p->K, count);
+    radon_kernel<<<grid, kSirtThreads, 0, st>>>(lin, sino, p->d_radon, p->N, p->K, p->M);
     return cudaGetLastError();
 }
 

@@ -1,4 +1,5 @@
-"""Algebraic reconstruction (SIRT on the fast Hough operators) on the GPU against the oracle.
+"""Algebraic reconstruction (SIRT on the fast Hough operators) and the fast Radon transform on
+the GPU against the oracle.
 
 Tolerances: the Hough-space data use the resampling's float32 positions and weights
 (compared at 1e-6 of the largest value); SIRT iterates float32 sums of the exact operators,
@@ -100,3 +101,33 @@ def test_sirt_rejects_bad_relaxation(fbp, torch):
     for lam in (0.0, 2.0, -1.0, float("nan")):
         with pytest.raises(RuntimeError):
             fbp.fbp_sirt(plan, b, img, 1, lam)
+
+
+@pytest.mark.parametrize("N", [2, 16, 64])
+def test_fast_radon_matches_oracle(fbp, torch, N):
+    import oracle.radon as orad
+    K, M = phantoms.geometry_for(N)
+    rng = np.random.default_rng(N + 9)
+    img = rng.random(size=(2, N, N)).astype(np.float32)
+    plan = fbp.fbp_plan(N, K, M, 2)
+    sino = torch.full(plan.sino_shape, float("nan"), device="cuda")
+    fbp.fbp_radon(plan, dev(torch, img), sino)
+    torch.cuda.synchronize()
+    got = sino.cpu().numpy()
+    for s in range(2):
+        want = orad.fast_radon(img[s].astype(np.float64), K, M)
+        assert np.abs(got[s] - want).max() <= 1e-5 * np.abs(want).max()
+
+
+def test_fast_radon_keeps_the_mass_at_512(fbp, torch):
+    N = 512
+    K, M = phantoms.geometry_for(N)
+    plan = fbp.fbp_plan(N, K, M, 2)
+    gen = torch.Generator(device="cuda").manual_seed(6)
+    img = torch.rand(plan.img_shape, device="cuda", generator=gen)
+    sino = torch.empty(plan.sino_shape, device="cuda")
+    fbp.fbp_radon(plan, img, sino)
+    torch.cuda.synchronize()
+    mass = sino.double().sum(dim=2)
+    total = img.double().sum(dim=(1, 2))
+    assert float((mass / total[:, None] - 1).abs().max()) < 1e-2

@@ -38,6 +38,9 @@ MISTAKES = [
     ("sirt.py", "(b - hough_project(f))", "(hough_project(f) - b)"),             # residual sign
     ("sirt.py", "scale = 1.0 / (row_weights(N) * np.sqrt(1.0 + sigma * sigma))",
      "scale = 1.0 / row_weights(N)"),                                         # no path length
+    # fast Radon transform
+    ("radon.py", "* np.sqrt(1.0 + sigma * sigma)", ""),                         # no path length
+    ("radon.py", "return 3, np.tan(theta - np.pi / 2)", "return 2, np.tan(theta - np.pi / 2)"),
 ]
 
 
@@ -55,6 +58,7 @@ def test_planted_mistake_is_caught(tmp_path, fname, old, new):
                         "tests/test_oracle_iir.py", "tests/test_oracle_geometry.py",
                         "tests/test_oracle_linogram.py", "tests/test_oracle_dyadic.py",
                         "tests/test_oracle_fbp.py", "tests/test_oracle_adjoint.py",
-                        "tests/test_oracle_cnn.py", "tests/test_oracle_sirt.py"],
+                        "tests/test_oracle_cnn.py", "tests/test_oracle_sirt.py",
+                        "tests/test_oracle_radon.py"],
                        cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, r.stdout[-2000:]
