@@ -22,13 +22,14 @@ adjoint    transposes of the filter, the resampling and the back projection (gra
            the fast method with respect to the sinogram)
 sirt       algebraic reconstruction (SIRT) on the fast Hough operators and the Hough-space
            data of a sinogram (Sec. 4.4)
+radon      the fast Radon transform: dyadic line sums (Eq. 17) resampled to (theta, r)
 cnn        the learned corrector's network, loss and gradients (an extension beside the
            paper's method)
 
 Readings of the paper that the oracle fixes where the text is silent or garbled are
 listed in each module's docstring.
 """
-from . import ramp, iir, geometry, linogram, dyadic, fbp, adjoint, sirt  # noqa: F401
+from . import ramp, iir, geometry, linogram, dyadic, fbp, adjoint, sirt, radon  # noqa: F401
 from .ramp import ramp_h, ramp_h_sinc, causal_part, anticausal_part  # noqa: F401
 from .iir import (iir_causal, iir_anticausal, iir_filter, iir_impulse_response,  # noqa: F401
                   fir_ramp)
