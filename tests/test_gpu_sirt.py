@@ -131,3 +131,38 @@ def test_fast_radon_keeps_the_mass_at_512(fbp, torch):
     mass = sino.double().sum(dim=2)
     total = img.double().sum(dim=(1, 2))
     assert float((mass / total[:, None] - 1).abs().max()) < 1e-2
+
+
+def test_radon_and_hough_data_chunks_equal_single_slices(fbp, torch):
+    N, B = 32, 3
+    K, M = phantoms.geometry_for(N)
+    rng = np.random.default_rng(8)
+    img = dev(torch, rng.random(size=(B, N, N)))
+    sino = dev(torch, rng.normal(size=(B, K, M)))
+    plan = fbp.fbp_plan(N, K, M, B)
+    fbp.fbp_set_chunk(plan, 2)
+    rad = torch.empty(plan.sino_shape, device="cuda")
+    hd = torch.empty(plan.lin_shape, device="cuda")
+    fbp.fbp_radon(plan, img, rad)
+    fbp.fbp_hough_data(plan, sino, hd)
+    one = fbp.fbp_plan(N, K, M, 1)
+    for s in range(B):
+        r1 = torch.empty(one.sino_shape, device="cuda")
+        h1 = torch.empty(one.lin_shape, device="cuda")
+        fbp.fbp_radon(one, img[s:s + 1].contiguous(), r1)
+        fbp.fbp_hough_data(one, sino[s:s + 1].contiguous(), h1)
+        torch.cuda.synchronize()
+        assert torch.equal(rad[s:s + 1], r1)
+        assert torch.equal(hd[s:s + 1], h1)
+
+
+def test_sirt_with_no_iterations_leaves_the_image(fbp, torch):
+    N = 16
+    K, M = phantoms.geometry_for(N)
+    plan = fbp.fbp_plan(N, K, M, 1)
+    b = torch.ones(plan.lin_shape, device="cuda")
+    img = torch.randn(plan.img_shape, device="cuda")
+    before = img.clone()
+    fbp.fbp_sirt(plan, b, img, 0, 1.0)
+    torch.cuda.synchronize()
+    assert torch.equal(img, before)
