@@ -435,7 +435,7 @@ def run_ours(args):
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
     """The CPU oracle as the reference arm: each step times a bounded sample of one slice
-    of the same workload (float64 recursive filter of 192 of 3072 rows, float64 linogram,
+    of the same workload (float64 recursive filter of 192 of the K rows, float64 linogram,
     dyadic-pattern back projection of 2 slopes per quarter) and extrapolates to slices/s."""
     import numpy as np
 
@@ -458,9 +458,10 @@ def run_reference(args):
         secs.append(oracle_sample(s64, N, b, a, taus_per_quarter=2, rows=192)["sec_per_slice"])
     wall = time.perf_counter() - t0
     v = 1.0 / statistics.mean(secs)
-    sample = ("per step, one N=2048 slice: float64 recursive filter of 192 of 3072 rows (x16), "
-              "float64 linogram of all four quarters, float64 dyadic-pattern back projection of "
-              "2 of 2048 slopes per quarter (x1024)")
+    rows = min(192, K)
+    sample = (f"per step, one N={N} slice: float64 recursive filter of {rows} of {K} rows "
+              f"(x{K / rows:g}), float64 linogram of all four quarters, float64 dyadic-pattern "
+              f"back projection of 2 of {N} slopes per quarter (x{N / 2:g})")
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT,
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(wall / args.steps * 1e3, 1), "higher_is_better": True,
