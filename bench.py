@@ -395,10 +395,11 @@ def run_ours(args):
         })
         cpu_baseline = {"value": round(1.0 / res["sec_per_slice"], 6), "unit": UNIT,
                         "cores": 1, "kind": "oracle",
-                        "sample": ("one N=2048 slice: float64 recursive filter of all 3072 rows, "
+                        "sample": (f"one N={N} slice: float64 recursive filter of all {K} rows, "
                                    "float64 linogram of all four quarters, float64 dyadic-pattern "
-                                   "back projection of 8 of 2048 slopes per quarter (scaled x256); "
-                                   f"host has {cpu_cores()} cores, numpy runs single-threaded"),
+                                   f"back projection of 8 of {N} slopes per quarter (scaled "
+                                   f"x{N / 8:g}); host has {cpu_cores()} cores, numpy runs "
+                                   "single-threaded"),
                         "work_seconds": round(work, 1)}
 
     line = {
