@@ -187,8 +187,8 @@ fbp_status fbp_reconstruct_adjoint(fbp_plan_t plan, const float* d_img_grad,
  * on images d_img [batch][N][N] (in: the starting image, e.g. zeros or the fast FBP; out:
  * the result) for data d_lin_data [batch][4][N][2N].  0 < lambda < 2 (else
  * FBP_ERR_INVALID_ARG); iters >= 0.  Float32.  The first call makes the plan's R^-1 and
- * C^-1 tables (one slice, 40 N^2 bytes) and uses both workspaces.  Errors as
- * fbp_reconstruct. */
+ * C^-1 tables (one slice, 40 N^2 bytes) on its stream: a later call on another stream must
+ * be ordered after it.  Uses both workspaces.  Errors as fbp_reconstruct. */
 fbp_status fbp_hough_data(fbp_plan_t plan, const float* d_sino, float* d_lin, void* stream);
 
 /* Fast (approximate) Radon transform: images d_img [batch][N][N] -> sinograms d_sino
