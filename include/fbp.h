@@ -20,13 +20,16 @@
  *     FBP_ERR_MISALIGNED) and must not overlap unless a call says so.  Rows need not be
  *     aligned.
  *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the legacy default
- *     stream).  Arguments are validated before anything is launched; a call that returns
- *     an error has launched nothing.  A CUDA launch failure returns FBP_ERR_CUDA.
+ *     stream).  Arguments are validated before anything is launched: a call that returns
+ *     FBP_ERR_INVALID_ARG, FBP_ERR_MISALIGNED or FBP_ERR_UNSUPPORTED has launched nothing.
+ *     A CUDA launch failure returns FBP_ERR_CUDA (earlier launches of the same call may
+ *     already be queued).
  *   - A plan is not thread-safe: calls on one plan must be issued from one host thread.
  *     Calls that use the plan's workspace must not overlap on the GPU (issue them on one
  *     stream, or order them with events).
- *   - No call throws; no call synchronises the device except fbp_plan_destroy and
- *     fbp_last_device_error.
+ *   - No call throws.  No call synchronises the device except fbp_plan_destroy,
+ *     fbp_last_device_error and the allocations a plan makes on first use (its workspace,
+ *     the adjoint workspace, the SIRT tables) or when a larger chunk needs a larger one.
  */
 #ifndef FBP_H
 #define FBP_H
