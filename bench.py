@@ -115,9 +115,15 @@ def byte_model(N: int, K: int, M: int, n1: int) -> dict:
     Img = 4 * N * N
     P = math.ceil(math.log2(N) / 6)
     G = 4 * 4 * g_needed_floats(N, n1)
+    # charge_8d: the pass plan's per-step bytes assigned to the kernels that fuse those
+    # steps -- filter 2S; resampling (S + Lin) plus the first Hough pass (2 Lin) for pass 1;
+    # the last Hough pass (Lin + Lin/2) and the quarter sum (Lin/2 + Img) split between the
+    # two second-pass launches, the image write charged to the v launch.
+    charge_8d = dict(iir=2 * S, pass1_resample=S + (2 * (P - 1) + 1) * Lin,
+                     pass2=Lin + Img, pass2_h=Lin)
     return dict(S=S, Lin=Lin, Img=Img, P=P, B_model=3 * S + (2 * P + 1) * Lin + Img,
                 compulsory=S + Img, iir=2 * S, pass1_resample=S + G, pass2=G // 2 + Img,
-                pass2_h=G // 2 + 2 * Img, G=G)
+                pass2_h=G // 2 + 2 * Img, G=G, charge_8d=charge_8d)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -211,6 +217,60 @@ def cpu_cores() -> int:
         return len(os.sched_getaffinity(0))
     except AttributeError:
         return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def _oracle_sample_worker(job):
+    path, N, b, a, taus = job
+    import numpy as np
+    s64 = np.array(np.load(path, mmap_mode="r"))
+    return oracle_sample(s64, N, np.array(b), np.array(a), taus_per_quarter=taus)["sec_per_slice"]
+
+
+def oracle_all_cores(s64, N, b, a, taus):
+    """The bounded oracle sample on every core at once, one slice per spawned process:
+    returns (slices/s of all processes together, processes, wall seconds)."""
+    import multiprocessing as mp
+
+    import numpy as np
+    cores = cpu_cores()
+    fd, path = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    np.save(path, s64)
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    try:
+        for k in saved:
+            os.environ[k] = "1"                    # one thread per process
+        ctx = mp.get_context("spawn")
+        t0 = time.perf_counter()
+        with ctx.Pool(cores) as pool:
+            secs = pool.map(_oracle_sample_worker, [(path, N, list(b), list(a), taus)] * cores)
+        wall = time.perf_counter() - t0
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+        os.unlink(path)
+    return sum(1.0 / t for t in secs), cores, wall
 
 
 # ----------------------------------------------------------------------------- traffic
@@ -351,17 +411,30 @@ def run_ours(args):
     for name in ("iir", "pass1_resample", "pass2", "pass2_h"):
         ms, n = prof[name]
         if n:
-            kern[name] = dict(ms_per_launch=ms / n, launches=n,
-                              bytes_per_launch=model[name] * per_launch_slices)
+            sec = ms / n / 1e3
+            rec = dict(ms_per_launch=ms / n, launches=n,
+                       charge_8d_bytes=model["charge_8d"][name] * per_launch_slices,
+                       own_bytes=model[name] * per_launch_slices,
+                       traffic=traffic_for(name, plan.chunk))
+            rec["frac_8d"] = rec["charge_8d_bytes"] / sec / 1e9 / hbm
+            rec["frac_own"] = rec["own_bytes"] / sec / 1e9 / hbm
+            rec["traffic_frac"] = None if rec["traffic"] is None else rec["traffic"] / sec / 1e9 / hbm
+            kern[name] = rec
     dom = max(kern, key=lambda k: kern[k]["ms_per_launch"] * kern[k]["launches"])
     dk = kern[dom]
-    achieved = dk["bytes_per_launch"] / (dk["ms_per_launch"] / 1e3) / 1e9
+    achieved = dk["charge_8d_bytes"] / (dk["ms_per_launch"] / 1e3) / 1e9
+    rnd = lambda v, d=4: None if v is None else round(v, d)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
-                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": traffic_for(dom, plan.chunk),
+                "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": dk["traffic"],
                 "peak_source": peak_src,
+                "achieved_basis": "pass-plan bytes of the steps the kernel fuses (x slices per launch)",
+                "traffic_frac": rnd(dk["traffic_frac"]), "frac_own_bytes": rnd(dk["frac_own"]),
                 "kernels": {k: {"ms_per_launch": round(v["ms_per_launch"], 5),
                                 "launches": v["launches"],
-                                "GB_per_s": round(v["bytes_per_launch"] / (v["ms_per_launch"] / 1e3) / 1e9, 1)}
+                                "frac_8d": rnd(v["frac_8d"]),
+                                "frac_own_bytes": rnd(v["frac_own"]),
+                                "traffic_bytes": v["traffic"],
+                                "traffic_frac": rnd(v["traffic_frac"])}
                             for k, v in kern.items()}}
     t_slice = ms_step / 1e3 / S
     pipeline = {"B_model_bytes_per_slice": model["B_model"],
@@ -393,14 +466,17 @@ def run_ours(args):
             "rmse_fp64_fast_vs_fp64_direct": float(np.sqrt(np.mean((f64 - d64) ** 2))),
             "max_abs_vs_fp64_fast_over_range": float(np.abs(fast_img[ys, xs] - f64).max() / rng_img),
         })
+        v_all, cores_all, wall_all = oracle_all_cores(s64, N, b, a, 8)
         cpu_baseline = {"value": round(1.0 / res["sec_per_slice"], 6), "unit": UNIT,
                         "cores": 1, "kind": "oracle",
                         "sample": (f"one N={N} slice: float64 recursive filter of all {K} rows, "
                                    "float64 linogram of all four quarters, float64 dyadic-pattern "
                                    f"back projection of 8 of {N} slopes per quarter (scaled "
-                                   f"x{N / 8:g}); host has {cpu_cores()} cores, numpy runs "
-                                   "single-threaded"),
-                        "work_seconds": round(work, 1)}
+                                   f"x{N / 8:g}); single-threaded numpy; value_all: the same "
+                                   "sample on every core at once, one slice per process"),
+                        "work_seconds": round(work, 1),
+                        "value_all": round(v_all, 6), "cores_all": cores_all,
+                        "wall_seconds_all": round(wall_all, 1), "cpu_model": cpu_model()}
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,

@@ -293,11 +293,15 @@ fbp_status fbp_volume_destroy(fbp_volume_t v);
  * FBP_STATIC_MAX_N (8 MiB), which every GPU that loads the library holds until the process
  * exits; slices are processed one after another through it.  No call allocates or frees
  * memory.  The first call on a device looks up the array's device address and sets the
- * kernels' shared-memory limits for that device, so make it before any stream capture.
+ * kernels' shared-memory limits for that device, so make it before any stream capture;
+ * with lazy module loading the driver may back the array with device memory only at that
+ * lookup, so the first call on a device can fail with FBP_ERR_OOM when the device is full
+ * (later calls cannot).
  * All calls share the array: calls that overlap on the GPU race (issue them on one stream
  * or order them with events).
  * Errors: FBP_ERR_UNSUPPORTED (N not a power of two in [2, FBP_STATIC_MAX_N]),
- * FBP_ERR_INVALID_ARG (count < 1, null pointer), FBP_ERR_MISALIGNED, FBP_ERR_CUDA. */
+ * FBP_ERR_INVALID_ARG (count < 1, null pointer), FBP_ERR_MISALIGNED, FBP_ERR_OOM (first
+ * call on a device only), FBP_ERR_CUDA. */
 #define FBP_STATIC_MAX_N 512
 fbp_status fbp_fht_backproject_static(int N, int count, const float* d_lin, float* d_img,
                                       void* stream);

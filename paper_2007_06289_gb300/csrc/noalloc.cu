@@ -12,7 +12,9 @@
 // address; the device address is obtained with cudaGetSymbolAddress once per device and
 // handed to the kernels.  That set-up (and the kernels' shared-memory opt-in) happens on
 // the first call on each device, with that device current, so the first call on a device
-// should come before any stream capture.  Calls that overlap on the GPU share the array
+// should come before any stream capture.  With lazy module loading the driver may back the
+// array with device memory only at that first lookup, so the first call on a device is the
+// one that can fail for lack of memory (reported as FBP_ERR_OOM); later calls cannot.  Calls that overlap on the GPU share the array
 // and race; issue them on one stream (or order them with events).
 #include <mutex>
 
@@ -69,9 +71,10 @@ extern "C" fbp_status fbp_fht_backproject_static(int N, int count, const float* 
     if (count < 1 || !d_lin || !d_img) return FBP_ERR_INVALID_ARG;
     if (((uintptr_t)d_lin & 15u) || ((uintptr_t)d_img & 15u)) return FBP_ERR_MISALIGNED;
     float* scratch = nullptr;
-    if (scratch_for_current_device(&scratch) != cudaSuccess) {
+    const cudaError_t se = scratch_for_current_device(&scratch);
+    if (se != cudaSuccess) {
         cudaGetLastError();
-        return FBP_ERR_CUDA;
+        return se == cudaErrorMemoryAllocation ? FBP_ERR_OOM : FBP_ERR_CUDA;
     }
     // The launchers read only the sizes and the pass split from the plan record; a
     // zero-initialised record on the stack allocates nothing.

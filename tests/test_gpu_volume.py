@@ -1,12 +1,16 @@
-"""Ragged volumes (slices of mixed sizes in one call) against the one-slice path.
+"""Ragged volumes (slices of mixed sizes in one call) against the float64 oracle and the
+one-slice path.
 
-Every image of a volume must equal, bit for bit, the image fbp_reconstruct gives for that
-slice alone with the same filter: grouping, pointer tables, per-group streams, graph
-capture and replay, and the autotuner's choices change the execution, never the sums.
+Every image of a volume must match the float64 oracle (sampled pixels of every size group,
+N = 256 .. 2048, within 1e-5 of the image range, before and after autotuning) and equal,
+bit for bit, the image fbp_reconstruct gives for that slice alone with the same filter:
+grouping, pointer tables, per-group streams, graph capture and replay, and the autotuner's
+choices change the execution, never the sums.
 """
 import numpy as np
 import pytest
 
+import oracle
 import phantoms
 
 pytestmark = pytest.mark.gpu
@@ -117,3 +121,47 @@ def test_volume_rejects_bad_items(fbp, torch):
         fbp.fbp_volume_create([(N, spare[1:1 + K * M].view(K, M), img)])
     with pytest.raises(ValueError):
         fbp.fbp_volume_create([(N, sino, img[:-1])])
+
+
+def test_volume_matches_oracle_at_every_size(fbp, torch):
+    # the ragged benchmark's sizes (N = 256 .. 2048, standard geometry), shuffled, with
+    # repeated sizes; graph capture and replay, then the autotuner's choices
+    from paper_2007_06289_gb300 import iir_fit
+    sizes = [2048, 256, 1024, 512, 2048, 256, 1024]
+    items = []
+    for i, N in enumerate(sizes):
+        K, M = phantoms.geometry_for(N)
+        sino = phantoms.phantom_stack_torch(N, 1, 900 + i, "cuda", K=K, M=M,
+                                            noise_i0=1e5)[0].contiguous()
+        items.append((N, sino, torch.full((N, N), float("nan"), device="cuda")))
+    for N in set(sizes):                           # the volume's filters are the table's
+        b, a = fbp.fbp_default_coeffs(N, 3)
+        wb, wa = iir_fit.coefficients(N, 3)
+        assert np.array_equal(b, wb) and np.array_equal(a, wa)
+    rng = np.random.default_rng(17)
+    want = []
+    for N, sino, _ in items:
+        ys, xs = rng.integers(0, N, 32), rng.integers(0, N, 32)
+        ys[:4] = [0, N - 1, 0, N - 1]
+        xs[:4] = [0, 0, N - 1, N - 1]
+        s64 = sino.cpu().numpy().astype(np.float64)
+        want.append((ys, xs, oracle.fast_fbp_pixels(s64, N, *iir_fit.coefficients(N, 3), ys, xs)))
+
+    def check(tag):
+        for (N, _, img), (ys, xs, w) in zip(items, want):
+            got = img.cpu().numpy()
+            assert np.isfinite(got).all(), (tag, N)
+            err = np.abs(got[ys, xs] - w).max() / (got.max() - got.min())
+            assert err <= 1e-5, (tag, N, err)
+
+    st = torch.cuda.Stream()
+    vol = fbp.fbp_volume_create(items, order=3, graph=True)
+    vol.run(st)
+    st.synchronize()
+    check("graph")
+    choices = vol.tune(st)
+    for _, _, img in items:
+        img.fill_(float("nan"))
+    vol.run(st)
+    st.synchronize()
+    check(f"tuned {choices}")

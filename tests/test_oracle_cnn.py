@@ -75,3 +75,52 @@ def test_zero_last_layer_is_the_identity():
     x = np.random.default_rng(3).normal(size=(5, 5))
     y, _ = cnn.forward(params, x)
     np.testing.assert_array_equal(y, x)
+
+
+def test_bf16_rounding_matches_torch_and_ties_to_even():
+    import torch
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=2000) * 10.0 ** rng.integers(-8, 8, 2000)
+    x = np.concatenate([x, [0.0, -0.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, -(1 + 2 ** -8), 255.0, 257.0]])
+    want = torch.tensor(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(cnn.bf16(x), want)
+    assert cnn.bf16(1 + 2 ** -8) == 1.0                  # tie -> even mantissa
+    assert cnn.bf16(1 + 3 * 2 ** -8) == 1 + 2 ** -6      # tie -> even mantissa
+    assert cnn.bf16(255.0) == 255.0 and cnn.bf16(257.0) == 256.0
+
+
+def test_bf16_storage_is_exact_on_integer_networks():
+    from cnn_inputs import int_images, int_params
+    rng = np.random.default_rng(5)
+    ps = int_params(3)
+    x = int_images(rng, (24, 24), 0.6)
+    gy = int_images(rng, (24, 24), 0.5)
+    y16, c16 = cnn.forward(ps, x, "bf16")
+    y64, c64 = cnn.forward(ps, x, "f64")
+    np.testing.assert_array_equal(y16, y64)
+    g16, gx16 = cnn.backward(ps, c16, gy, "bf16")
+    g64, gx64 = cnn.backward(ps, c64, gy, "f64")
+    for (a, b), (c, d) in zip(g16, g64):
+        np.testing.assert_array_equal(a, c)
+        np.testing.assert_array_equal(b, d)
+    np.testing.assert_array_equal(gx16, gx64)
+    assert max(np.abs(h).max() for h in c16[1:]) <= 256
+
+
+def test_bf16_storage_rounds_the_stored_values():
+    rng = np.random.default_rng(6)
+    ps = cnn.init_params(channels=8, seed=2, scale=2.0)
+    ps = [(w, rng.normal(0, 0.1, size=b.shape)) for w, b in ps]
+    x = rng.normal(size=(10, 11))
+    y16, c16 = cnn.forward(ps, x, "bf16")
+    y64, _ = cnn.forward(ps, x, "f64")
+    for h in c16[1:]:                                   # stored hidden activations
+        np.testing.assert_array_equal(cnn.bf16(h), h)
+    assert 0 < np.abs(y16 - y64).max() <= 0.05 * np.abs(y64 - x).max()
+    gy = rng.normal(size=x.shape)
+    g16, _ = cnn.backward(ps, c16, gy, "bf16")
+    # a hidden layer's weight gradient is a sum of products of stored (bfloat16) values:
+    # planting float64 gradients in the bfloat16 pass changes it
+    g64, _ = cnn.backward(ps, c16, gy, "f64")
+    assert not np.array_equal(g16[2][0], g64[2][0])
+    assert np.abs(g16[2][0] - g64[2][0]).max() <= 0.05 * np.abs(g64[2][0]).max()

@@ -29,10 +29,12 @@ MISTAKES = [
     ("adjoint.py", "return np.stack([g, g[:, ::-1], g.T, g[::-1, :].T])",
      "return np.stack([g, g[:, ::-1], g, g[::-1, :].T])"),                    # missing transpose
     # CNN corrector
-    ("cnn.py", "xp[:, dy:dy + H, dx:dx + W])\n    return out",
-     "xp[:, 2 - dy:2 - dy + H, 2 - dx:2 - dx + W])\n    return out"),         # convolution, not correlation
+    ("cnn.py", "xp[:, dy:dy + H, dx:dx + W],\n                             optimize=True)\n    return out",
+     "xp[:, 2 - dy:2 - dy + H, 2 - dx:2 - dx + W],\n                             optimize=True)\n    return out"),  # convolution, not correlation
     ("cnn.py", "gh = gin * (hin > 0.0)", "gh = gin"),                          # ReLU mask dropped
     ("cnn.py", "return x + h[0], cache", "return h[0], cache"),                 # no skip connection
+    ("cnn.py", "u = (u + 0x7FFF + ((u >> 16) & 1))", "u = (u + 0x8000)"),      # ties away from even
+    ("cnn.py", "                h = bf16(h)\n", ""),                            # activations not stored in bf16
     # algebraic reconstruction
     ("sirt.py", "f = f + lam * cinv * back_project(", "f = f + lam * back_project("),  # no C^-1
     ("sirt.py", "(b - hough_project(f))", "(hough_project(f) - b)"),             # residual sign

@@ -15,7 +15,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("N", [8, 64, 256, 512])
+@pytest.mark.parametrize("N", [2, 4, 8, 64, 256, 512])
 def test_static_scratch_matches_planned_backprojection_twice(fbp, N):
     import torch
     lib = fbp.load_library()
@@ -43,3 +43,24 @@ def test_static_scratch_rejects_sizes_beyond_its_limit(fbp):
     assert lib.fbp_fht_backproject_static(1024, 1, p, p, None) == 2     # N above the maximum
     assert lib.fbp_fht_backproject_static(48, 1, p, p, None) == 2       # not a power of two
     assert lib.fbp_fht_backproject_static(64, 0, p, p, None) == 1       # empty batch
+
+
+def test_static_scratch_allocates_nothing(fbp):
+    # After one warm-up call (which may make the driver back the fixed array and load the
+    # kernels), further calls leave the device's free memory unchanged.
+    import torch
+    lib = fbp.load_library()
+    N = 512
+    lin = torch.zeros((3, 4, N, 2 * N), device="cuda")
+    img = torch.empty((3, N, N), device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    args = (N, 3, ctypes.c_void_p(lin.data_ptr()), ctypes.c_void_p(img.data_ptr()),
+            ctypes.c_void_p(stream))
+    assert lib.fbp_fht_backproject_static(*args) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert lib.fbp_fht_backproject_static(*args) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
