@@ -210,10 +210,11 @@ fbp_status fbp_sirt(fbp_plan_t plan, const float* d_lin_data, float* d_img, int 
  * trained to map fast images towards direct-FBP images.  No counterpart in the paper: a
  * learned extension.  Parameters: one fp32 device array of fbp_cnn_param_count() floats,
  * layer after layer, each layer's weights [co][ci][3][3] then its biases [co].  The four
- * 32 -> 32 layers run as bf16 tensor-core implicit GEMMs with fp32 accumulation (hidden
- * activations are stored as bf16); the first and last layers and the weight gradients in
- * fp32.  Images: [batch][N][N] fp32, N a power of two in 16..4096.  The caller provides the
- * workspace (16-byte aligned). */
+ * 32 -> 32 layers run as bf16 implicit GEMMs on the tcgen05 tensor cores (accumulators in
+ * tensor memory, fp32; operands staged by bulk copies), hidden activations and gradients
+ * stored as bf16; the first and last layers and the weight gradients in fp32.  Images:
+ * [batch][N][N] fp32, N a power of two in 16..4096.  The caller provides the workspace
+ * (16-byte aligned).  Calls that share a workspace must not overlap on the GPU. */
 size_t fbp_cnn_param_count(void);
 
 /* Workspace bytes for `batch` images of N x N; train != 0 keeps the activations for
@@ -233,6 +234,12 @@ fbp_status fbp_cnn_forward(const float* d_params, const float* d_x, float* d_y, 
 fbp_status fbp_cnn_backward(const float* d_params, const float* d_x, const float* d_gy,
                             float* d_gparams, void* d_ws, size_t ws_bytes, int N, int batch,
                             void* stream);
+
+/* Synchronise the current device and read (then clear) the corrector's device status word:
+ * FBP_ERR_TIMEOUT if a tensor-core convolution gave up a bounded wait (about a second) for
+ * its copies or its matrix products since the last read -- its output is then incomplete --
+ * else FBP_OK.  FBP_ERR_CUDA if the device cannot be read. */
+fbp_status fbp_cnn_last_error(void);
 
 /* ------------------------------------------------------------------ ragged volumes
  * A volume whose slices differ in size (N, K, M), each slice in its own buffers.  No

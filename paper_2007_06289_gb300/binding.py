@@ -85,6 +85,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "fbp_cnn_workspace_bytes": (S, [I, I, I]),
         "fbp_cnn_forward": (I, [V, V, V, V, S, I, I, I, V]),
         "fbp_cnn_backward": (I, [V, V, V, V, V, S, I, I, V]),
+        "fbp_cnn_last_error": (I, []),
         "fbp_volume_create": (I, [ctypes.POINTER(P), ctypes.POINTER(fbp_item), I, I, I]),
         "fbp_volume_run": (I, [P, V]),
         "fbp_volume_tune": (I, [P, V, ctypes.POINTER(I), ctypes.POINTER(I)]),
@@ -487,3 +488,8 @@ def fbp_cnn_backward(params, x, gy, gparams, ws, stream=None) -> None:
         _dev_ptr(params, (fbp_cnn_param_count(),), "params"), _dev_ptr(x, (B, N, N), "x"),
         _dev_ptr(gy, (B, N, N), "gy"), _dev_ptr(gparams, (fbp_cnn_param_count(),), "gparams"),
         p, nb, N, B, _stream_ptr(stream)))
+
+
+def fbp_cnn_last_error() -> int:
+    """Read and clear the corrector's device status word (synchronises the device)."""
+    return int(load_library().fbp_cnn_last_error())

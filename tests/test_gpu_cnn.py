@@ -18,9 +18,10 @@ Two kinds of parity:
   relative L2 the output stays within 2e-3 of the bfloat16 oracle; the weight gradients,
   sums of many products whose stored factors each carry such moved decisions from up to
   four layers below, within 2^-6.  Against the plain float64 network (no bfloat16 stores)
-  the output stays within 3e-2 in relative L2 and the weight gradients within 2^-3: the first
-  layer's gradient sums values that passed four bfloat16 stores, which alone moves it by
-  ~9% at N = 128.
+  the output stays within 3e-2 in relative L2.  The gradients are not compared with it: the
+  first layer's gradients sum values that passed four bfloat16 stores, which alone moves
+  them by 9% (weights) to 15% (biases) at N = 128 -- a property of the storage precision,
+  which the bfloat16 oracle reproduces.
 """
 import numpy as np
 import pytest
@@ -63,6 +64,7 @@ def run_gpu(fbp, torch, flat, x, gy=None):
         g = torch.full_like(params, float("nan"))
         fbp.fbp_cnn_backward(params, xd, torch.tensor(gy.astype(np.float32), device="cuda"), g, ws)
     torch.cuda.synchronize()
+    assert fbp.fbp_cnn_last_error() == 0
     return y.cpu().numpy().astype(np.float64), (None if g is None else g.cpu().numpy().astype(np.float64))
 
 
@@ -124,16 +126,12 @@ def test_gradients_match_oracle_elementwise(fbp, torch):
     _, g = run_gpu(fbp, torch, flat, x, gy)
     ps = unflatten(flat)
     want16 = np.zeros(g.size)
-    want64 = np.zeros(g.size)
     bound = np.zeros(g.size)
     for b in range(B):
         _, c16 = ocnn.forward(ps, x[b], "bf16")
         g16, _ = ocnn.backward(ps, c16, gy[b], "bf16")
         want16 += flatten(g16)
         bound += flatten(abs_gradient_bound(ocnn, ps, c16, gy[b]))
-        _, c64 = ocnn.forward(ps, x[b], "f64")
-        g64, _ = ocnn.backward(ps, c64, gy[b], "f64")
-        want64 += flatten(g64)
     err = np.abs(g - want16)
     assert np.all(err <= 5 * U7 * bound + 1e-6 * np.abs(want16).max())
     off = 0
@@ -142,8 +140,6 @@ def test_gradients_match_oracle_elementwise(fbp, torch):
         sl_w, sl_b = slice(off, off + w.size), slice(off + w.size, off + n)
         assert rel(g[sl_w], want16[sl_w]) <= 2.0 ** -6, k
         assert rel(g[sl_b], want16[sl_b]) <= 2.0 ** -6, k
-        assert rel(g[sl_w], want64[sl_w]) <= 2.0 ** -3, k
-        assert rel(g[sl_b], want64[sl_b]) <= 2.0 ** -3, k
         off += n
 
 
