@@ -351,8 +351,13 @@ fbp_status fbp_profile_read(fbp_plan_t plan, int kernel, double* total_ms, long 
 /* Static text for a status code. */
 const char* fbp_status_str(fbp_status status);
 
-/* Synchronise the plan's device and read (then clear) the plan's device status word, set
- * by kernels whose bounded waits or consistency checks failed.  FBP_OK if none. */
+/* Synchronise the plan's device and read (then clear) the plan's device status word:
+ * FBP_ERR_INTERNAL when a kernel rejected a geometry-table row naming an angle row outside
+ * the sinogram (checked in every build; the row is resampled as zeros) or, in the library
+ * built with FBP_BOUNDS_CHECK (libfbp_checked.so, include/fbp_check.h), an index outside its
+ * buffer or Hough tile (the access is skipped); FBP_OK if none since the last read.  The
+ * plan's kernels never wait on one another, so FBP_ERR_TIMEOUT does not occur here (the
+ * corrector's bounded waits report through fbp_cnn_last_error). */
 fbp_status fbp_last_device_error(fbp_plan_t plan);
 
 #ifdef __cplusplus

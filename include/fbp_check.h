@@ -1,0 +1,29 @@
+/* Test hook of the bounds-checked build of libfbp (libfbp_checked.so, compiled with
+ * FBP_BOUNDS_CHECK); the ordinary library does not export it.  No counterpart in the paper.
+ *
+ * In the checked build every pipeline kernel checks each global index it forms against its
+ * buffer and the shared-memory range of each Hough round; every build checks that each
+ * geometry-table row it uses names angle rows inside the sinogram.  A failed check skips the
+ * access and records FBP_ERR_INTERNAL in the plan's status word (fbp_last_device_error). */
+#ifndef FBP_CHECK_H
+#define FBP_CHECK_H
+
+#include "fbp.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Overwrite the first angle row k0 of geometry-table row (quarter q, slope row i) of the
+ * plan (synchronises the device first).  With k0 outside [0, K-1] (or not K-1 on the row
+ * that wraps past the last angle) the kernels reject that row: they validate it before any
+ * access, resample it as zeros and set the status word.  For tests of the status word; the
+ * plan's results are meaningless afterwards.
+ * Errors: FBP_ERR_INVALID_ARG (NULL plan, q outside 0..3, i outside 0..N-1), FBP_ERR_CUDA. */
+fbp_status fbp_check_set_row_angle(fbp_plan_t plan, int q, int i, int k0);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FBP_CHECK_H */

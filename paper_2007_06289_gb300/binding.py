@@ -13,7 +13,9 @@ import re
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfbp.so")
+CHECKED_LIB_PATH = os.path.join(_HERE, "libfbp_checked.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "fbp.h")
+CHECK_HEADER = os.path.join(os.path.dirname(_HERE), "include", "fbp_check.h")
 MAX_ORDER = 8
 
 _STATUS = {0: "FBP_OK", 1: "FBP_ERR_INVALID_ARG", 2: "FBP_ERR_UNSUPPORTED",
@@ -48,7 +50,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     global _lib
     if _lib is not None:
         return _lib
-    path = path or LIB_PATH
+    # FBP_LIBRARY names another build of the library (the bounds-checked one, in tests)
+    path = path or os.environ.get("FBP_LIBRARY") or LIB_PATH
     if not os.path.exists(path):
         raise ImportError(f"libfbp.so not found at {path}; build it with "
                           "paper_2007_06289_gb300.build.build()")
@@ -94,6 +97,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "fbp_volume_destroy": (I, [P]),
         "fbp_last_device_error": (I, [P]),
     }
+    if hasattr(lib, "fbp_check_set_row_angle"):           # bounds-checked build only
+        sig["fbp_check_set_row_angle"] = (I, [P, I, I, I])
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
         fn.restype = res
@@ -493,3 +498,9 @@ def fbp_cnn_backward(params, x, gy, gparams, ws, stream=None) -> None:
 def fbp_cnn_last_error() -> int:
     """Read and clear the corrector's device status word (synchronises the device)."""
     return int(load_library().fbp_cnn_last_error())
+
+
+def fbp_check_set_row_angle(plan: Plan, q: int, i: int, k0: int) -> None:
+    """Test hook of the bounds-checked library (include/fbp_check.h)."""
+    _check("fbp_check_set_row_angle",
+           load_library().fbp_check_set_row_angle(plan.handle, int(q), int(i), int(k0)))

@@ -25,9 +25,10 @@
 // CTA roles (persistent, one CTA per SM): warp 0 lane 0 issues the bulk copies of each
 // tile's 12 runs into a 6-stage ring (mbarrier with transaction bytes); warp 1 owns the TMEM
 // allocation and its lane 0 issues the MMAs and commits them to the stage's "empty" and the
-// accumulator's "full" barriers; warps 2-5 (one per TMEM lane quarter) read the
-// accumulators with tcgen05.ld, add bias, apply ReLU or the backward mask, and store the
-// tile's four planes as 16-byte records (zero for pad records).  Every wait is bounded
+// accumulator's "full" barriers; two epilogue warpgroups (warps 2-5 and 6-9, each warp one
+// TMEM lane quarter) take alternate tiles from four accumulators, read them with
+// tcgen05.ld, add bias, apply ReLU or the backward mask, and store the tile's four planes as
+// 16-byte records (zero for pad records).  Every wait is bounded
 // (about a second); on expiry the CTA sets the corrector's status word, the other roles
 // leave their loops, outstanding copies and MMAs are waited for, and TMEM is freed.
 //
@@ -58,8 +59,10 @@ constexpr int kStageBytes = 3 * kPlanes * kRunBytes;       // 24960
 constexpr int kStages = 6;
 constexpr int kWChunks = kTaps * kPlanes;                  // 36 K chunks of 8
 constexpr int kWBytes = kWChunks * kC * 16;                // 18432
-constexpr int kConvThreads = 192;
-constexpr int kBarriers = 2 * kStages + 4 + 2;
+constexpr int kAcc = 4;           // TMEM accumulators (32 columns each)
+constexpr int kEpiGroups = 2;     // epilogue warpgroups; group g takes the tiles i = g mod 2
+constexpr int kConvThreads = 64 + 128 * kEpiGroups;
+constexpr int kBarriers = 2 * kStages + 2 * kAcc + 2;
 constexpr size_t kConvSmem = (size_t)kWBytes + (size_t)kStages * kStageBytes + kBarriers * 8 + 16;
 constexpr int kTileY = 8, kTileX = 16;           // pixels per tile of the weight-gradient kernel
 constexpr int kHaloY = kTileY + 2, kHaloX = kTileX + 2;
@@ -274,9 +277,9 @@ cnn_conv32_kernel(ConvArgs a)
     uint64_t* bars = reinterpret_cast<uint64_t*>(stages + (size_t)kStages * kStageBytes);
     uint64_t* full = bars;                  // [kStages] runs landed
     uint64_t* empty = bars + kStages;       // [kStages] runs consumed by the MMAs
-    uint64_t* tfull = bars + 2 * kStages;   // [2] accumulator complete
-    uint64_t* tempty = tfull + 2;           // [2] accumulator read out
-    uint64_t* wbar = tempty + 2;            // weights landed
+    uint64_t* tfull = bars + 2 * kStages;   // [kAcc] accumulator complete
+    uint64_t* tempty = tfull + kAcc;        // [kAcc] accumulator read out
+    uint64_t* wbar = tempty + kAcc;         // weights landed
     uint64_t* drain = wbar + 1;             // MMAs of this CTA complete (exit)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -290,7 +293,7 @@ cnn_conv32_kernel(ConvArgs a)
             mbar_init(full + s, 1);
             mbar_init(empty + s, 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kAcc; ++b) {
             mbar_init(tfull + b, 1);
             mbar_init(tempty + b, 4);
         }
@@ -300,8 +303,8 @@ cnn_conv32_kernel(ConvArgs a)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;"
-                     ::"r"(smem_u32(tmem_slot)) : "memory");
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "n"(kAcc * kC) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
@@ -315,12 +318,15 @@ cnn_conv32_kernel(ConvArgs a)
             mbar_expect_tx(wbar, kWBytes);
             bulk_g2s(wsm, a.wimg, kWBytes, wbar);
             long long i = 0;
+            int img = (int)(blockIdx.x / G.T), tt = (int)(blockIdx.x % G.T);
             for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i) {
                 const int s = (int)(i % kStages);
                 const uint32_t k = (uint32_t)(i / kStages);
+                if (i > 0) {                               // next tile of this CTA
+                    tt += gridDim.x;
+                    while (tt >= G.T) { tt -= G.T; ++img; }
+                }
                 if (!wait_bar(empty + s, (k & 1u) ^ 1u, abort_flag)) break;
-                const int img = (int)(t / G.T);
-                const int tt = (int)(t - (long long)img * G.T);
                 const long long m0 = kRecGuard + G.W + (long long)kTileM * tt;
                 mbar_expect_tx(full + s, kStageBytes);
                 unsigned char* dst = stages + (size_t)s * kStageBytes;
@@ -349,8 +355,8 @@ cnn_conv32_kernel(ConvArgs a)
                 for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i) {
                     const int s = (int)(i % kStages);
                     const uint32_t k = (uint32_t)(i / kStages);
-                    const int b = (int)(i & 1);
-                    const uint32_t j = (uint32_t)(i >> 1);
+                    const int b = (int)(i % kAcc);
+                    const uint32_t j = (uint32_t)(i / kAcc);
                     if (!wait_bar(full + s, k & 1u, abort_flag)) break;
                     if (!wait_bar(tempty + b, (j & 1u) ^ 1u, abort_flag)) break;
                     tc_fence_after();
@@ -375,16 +381,19 @@ cnn_conv32_kernel(ConvArgs a)
             drain_bar(drain, 0);                // ... once this phase does
         }
     } else {
-        // ---- epilogue: warps 2..5 read TMEM lane quarters (warp % 4)
+        // ---- epilogue: warpgroup eg (warps 2+4eg .. 5+4eg) takes tiles i = eg mod 2; each
+        // warp reads TMEM lane quarter warp % 4
         const int q = warp & 3;
         const int row = 32 * q + lane;
-        const int etid = threadIdx.x - 64;               // 0 .. 127
+        const int eg = (warp - 2) >> 2;
+        const int etid = threadIdx.x - 64;               // 0 .. 128 kEpiGroups - 1
         // zero the records no tile writes: the guard and top pad row, and the tail
         const long long head = kRecGuard + G.W;
         const long long tail0 = kRecGuard + G.W + (long long)kTileM * G.T;
         const long long tail = G.plane - tail0;
         const long long nz = (long long)a.images * kPlanes * (head + tail);
-        for (long long z = (long long)blockIdx.x * 128 + etid; z < nz; z += (long long)gridDim.x * 128) {
+        for (long long z = (long long)blockIdx.x * (128 * kEpiGroups) + etid; z < nz;
+             z += (long long)gridDim.x * (128 * kEpiGroups)) {
             const long long pl = z / (head + tail);
             const long long r = z - pl * (head + tail);
             a.out[pl * G.plane + (r < head ? r : tail0 + (r - head))] = make_uint4(0u, 0u, 0u, 0u);
@@ -392,10 +401,18 @@ cnn_conv32_kernel(ConvArgs a)
         float bias[kC];
 #pragma unroll
         for (int c = 0; c < kC; ++c) bias[c] = BIAS ? __ldg(a.bias + c) : 0.0f;
-        long long i = 0;
-        for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i) {
-            const int b = (int)(i & 1);
-            const uint32_t j = (uint32_t)(i >> 1);
+        long long i = eg;
+        int img = (int)((blockIdx.x + (long long)eg * gridDim.x) / G.T);
+        int tt = (int)((blockIdx.x + (long long)eg * gridDim.x) % G.T);
+        const int step = kEpiGroups * gridDim.x;
+        for (long long t = blockIdx.x + (long long)eg * gridDim.x; t < total;
+             t += step, i += kEpiGroups) {
+            if (i != eg) {                               // next tile of this warpgroup
+                tt += step;
+                while (tt >= G.T) { tt -= G.T; ++img; }
+            }
+            const int b = (int)(i % kAcc);
+            const uint32_t j = (uint32_t)(i / kAcc);
             if (!wait_bar(tfull + b, j & 1u, abort_flag)) break;
             tc_fence_after();
             uint32_t v[32];
@@ -403,12 +420,12 @@ cnn_conv32_kernel(ConvArgs a)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty + b);
-            const int img = (int)(t / G.T);
-            const int tt = (int)(t - (long long)img * G.T);
-            const long long m = kRecGuard + G.W + (long long)kTileM * tt + row;
-            const long long rel = m - kRecGuard;
-            const int y = (int)(rel / G.W) - 1;
-            const int x = (int)(rel - (long long)(y + 1) * G.W) - 1;
+            // pixel of this record: 32-bit arithmetic (a plane has < 2^31 records)
+            const unsigned rel = (unsigned)(G.W + kTileM * tt + row);
+            const unsigned yy = rel / (unsigned)G.W;
+            const int y = (int)yy - 1;
+            const int x = (int)(rel - yy * (unsigned)G.W) - 1;
+            const long long m = kRecGuard + (long long)rel;
             const bool inside = (unsigned)y < (unsigned)a.N && (unsigned)x < (unsigned)a.N;
             float mk[kC];
             if (MASK && inside) {
@@ -439,55 +456,79 @@ cnn_conv32_kernel(ConvArgs a)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kAcc * kC) : "memory");
     }
 }
 
 // ---------------------------------------------------------------- 1 -> 32 and 32 -> 1
 // First layer: h[p][o] = relu(b[o] + sum_tap w[o][tap] x[p + off(tap)]), fp32 math, written
-// as records over the whole plane (zero outside the image).
-__global__ void __launch_bounds__(256)
+// as records over the whole plane (zero outside the image).  The weights sit in shared
+// memory as [tap][o] and reach registers as 16-byte broadcasts, 32 per tap; each thread
+// computes the records r and r + kFirstStride.
+constexpr int kFirstStride = 128;           // records between a thread's two records
+__global__ void __launch_bounds__(128)
 cnn_first_kernel(const float* __restrict__ x, const float* __restrict__ w,
                  uint4* __restrict__ h, int N)
 {
-    __shared__ float ws[kC * kTaps + kC];
-    for (int e = threadIdx.x; e < kC * kTaps + kC; e += blockDim.x) ws[e] = w[e];  // w then b
+    __shared__ __align__(16) float ws[kTaps][kC];
+    __shared__ float bs[kC];
+    for (int e = threadIdx.x; e < kC * kTaps; e += blockDim.x) ws[e % kTaps][e / kTaps] = w[e];
+    for (int e = threadIdx.x; e < kC; e += blockDim.x) bs[e] = w[kC * kTaps + e];
     __syncthreads();
     const ActGeom G = act_geom(N);
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= G.plane) return;
+    const long long r0 = (long long)blockIdx.x * 2 * kFirstStride + threadIdx.x;
     const int img = blockIdx.y;
-    const long long rel = r - kRecGuard;
-    const int py = rel >= 0 ? (int)(rel / G.W) - 1 : -2;
-    const int px = rel >= 0 ? (int)(rel - (long long)(py + 1) * G.W) - 1 : -2;
-    uint4* dst = h + (long long)img * kPlanes * G.plane + r;
-    if ((unsigned)py >= (unsigned)N || (unsigned)px >= (unsigned)N) {
-#pragma unroll
-        for (int p = 0; p < kPlanes; ++p) dst[p * G.plane] = make_uint4(0u, 0u, 0u, 0u);
-        return;
-    }
     const float* xs = x + (size_t)img * N * N;
-    float v[kTaps];
+    float v[2][kTaps];
+    bool inside[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const long long r = r0 + u * kFirstStride;
+        int py = -2, px = -2;                   // pixel of record r (32-bit: r < 2^31)
+        if (r >= kRecGuard && r < G.plane) {
+            const unsigned q = (unsigned)(r - kRecGuard);
+            const unsigned yy = q / (unsigned)G.W;
+            py = (int)yy - 1;
+            px = (int)(q - yy * (unsigned)G.W) - 1;
+        }
+        inside[u] = (unsigned)py < (unsigned)N && (unsigned)px < (unsigned)N;
+#pragma unroll
+        for (int tap = 0; tap < kTaps; ++tap) {
+            const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
+            v[u][tap] = (inside[u] && yy >= 0 && yy < N && xx >= 0 && xx < N) ? xs[(size_t)yy * N + xx] : 0.0f;
+        }
+    }
+    float acc[2][kC];
+#pragma unroll
+    for (int o = 0; o < kC; ++o) acc[0][o] = acc[1][o] = bs[o];
 #pragma unroll
     for (int tap = 0; tap < kTaps; ++tap) {
-        const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
-        v[tap] = (yy >= 0 && yy < N && xx >= 0 && xx < N) ? xs[(size_t)yy * N + xx] : 0.0f;
-    }
 #pragma unroll
-    for (int p = 0; p < kPlanes; ++p) {
-        uint32_t w4[4];
+        for (int o4 = 0; o4 < kC; o4 += 4) {
+            const float4 wv = *reinterpret_cast<const float4*>(&ws[tap][o4]);
+            const float wk[4] = {wv.x, wv.y, wv.z, wv.w};
 #pragma unroll
-        for (int hh = 0; hh < 4; ++hh) {
-            const int o = 8 * p + 2 * hh;
-            float s0 = ws[kC * kTaps + o], s1 = ws[kC * kTaps + o + 1];
-#pragma unroll
-            for (int tap = 0; tap < kTaps; ++tap) {
-                s0 = fmaf(ws[o * kTaps + tap], v[tap], s0);
-                s1 = fmaf(ws[(o + 1) * kTaps + tap], v[tap], s1);
+            for (int k = 0; k < 4; ++k) {
+                acc[0][o4 + k] = fmaf(wk[k], v[0][tap], acc[0][o4 + k]);
+                acc[1][o4 + k] = fmaf(wk[k], v[1][tap], acc[1][o4 + k]);
             }
-            w4[hh] = pack_bf16(fmaxf(s0, 0.0f), fmaxf(s1, 0.0f));
         }
-        dst[p * G.plane] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+    }
+    uint4* dst = h + (long long)img * kPlanes * G.plane;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const long long r = r0 + u * kFirstStride;
+        if (r >= G.plane) continue;
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            uint32_t w4[4];
+#pragma unroll
+            for (int hh = 0; hh < 4; ++hh) {
+                const int o = 8 * p + 2 * hh;
+                w4[hh] = inside[u] ? pack_bf16(fmaxf(acc[u][o], 0.0f), fmaxf(acc[u][o + 1], 0.0f)) : 0u;
+            }
+            dst[p * G.plane + r] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
     }
 }
 
@@ -499,29 +540,54 @@ __device__ __forceinline__ void load_pixel32(float (&v)[kC], const uint4* planes
     for (int p = 0; p < kPlanes; ++p) unpack_record(planes[p * plane + r], v + 8 * p);
 }
 
-// Last layer and the skip connection: y[p] = x[p] + b + sum_{tap, c} w[c][tap] h[p + off][c]
-// (pad records are zero: no bounds tests).
-__global__ void __launch_bounds__(256)
+// Last layer and the skip connection: y[p] = x[p] + b + sum_{tap, c} w[c][tap] h[p + off][c].
+// One 16 x 16 output tile per CTA: its 18 x 18 records (four planes) are staged in shared
+// memory once; the weights sit there as [tap][c] and reach registers as 16-byte broadcasts;
+// each thread sums the 9 taps x 32 channels of two pixels, rows ly and ly + 8 (pad records
+// are zero: no bounds tests).
+constexpr int kLT = 16;
+constexpr int kLH = kLT + 2;
+__global__ void __launch_bounds__(kLT * kLT / 2)
 cnn_last_kernel(const float* __restrict__ x, const uint4* __restrict__ h, const float* __restrict__ w,
                 float* __restrict__ y, int N)
 {
-    __shared__ float ws[kC * kTaps + 1];
-    for (int e = threadIdx.x; e < kC * kTaps + 1; e += blockDim.x) ws[e] = w[e];   // w then b
-    __syncthreads();
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= N * N) return;
+    __shared__ __align__(16) float ws[kTaps][kC];
+    __shared__ uint4 hs[kPlanes][kLH * kLH];
+    for (int e = threadIdx.x; e < kC * kTaps; e += blockDim.x) ws[e % kTaps][e / kTaps] = w[e];
+    const float bias = w[kC * kTaps];
     const ActGeom G = act_geom(N);
-    const int py = p / N, px = p - py * N;
-    const size_t img = (size_t)blockIdx.y * N * N;
+    const int tiles_x = N / kLT;
+    const int y0 = (int)(blockIdx.x / tiles_x) * kLT, x0 = (int)(blockIdx.x % tiles_x) * kLT;
     const uint4* hp = h + (long long)blockIdx.y * kPlanes * G.plane;
-    float s = ws[kC * kTaps];
-    for (int tap = 0; tap < kTaps; ++tap) {
-        float v[kC];
-        load_pixel32(v, hp, G.plane, rec_index(G, py + tap / 3 - 1, px + tap % 3 - 1));
-#pragma unroll
-        for (int c = 0; c < kC; ++c) s = fmaf(ws[c * kTaps + tap], v[c], s);
+    for (int e = threadIdx.x; e < kPlanes * kLH * kLH; e += blockDim.x) {
+        const int p = e / (kLH * kLH), r = e - p * (kLH * kLH);
+        const int ty = r / kLH, tx = r - ty * kLH;
+        hs[p][r] = hp[p * G.plane + rec_index(G, y0 - 1 + ty, x0 - 1 + tx)];
     }
-    y[img + p] = x[img + p] + s;
+    __syncthreads();
+    const int ly = threadIdx.x / kLT, lx = threadIdx.x % kLT;      // rows ly and ly + 8
+    float s0 = bias, s1 = bias;
+    for (int tap = 0; tap < kTaps; ++tap) {
+        const int r = (ly + tap / 3) * kLH + lx + tap % 3;
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            float v0[8], v1[8];
+            unpack_record(hs[p][r], v0);
+            unpack_record(hs[p][r + (kLT / 2) * kLH], v1);
+            const float4 wa = *reinterpret_cast<const float4*>(&ws[tap][8 * p]);
+            const float4 wb = *reinterpret_cast<const float4*>(&ws[tap][8 * p + 4]);
+            const float wk[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                s0 = fmaf(wk[e], v0[e], s0);
+                s1 = fmaf(wk[e], v1[e], s1);
+            }
+        }
+    }
+    const size_t pix = (size_t)blockIdx.y * N * N + (size_t)(y0 + ly) * N + x0 + lx;
+    y[pix] = x[pix] + s0;
+    const size_t pix1 = pix + (size_t)(kLT / 2) * N;
+    y[pix1] = x[pix1] + s1;
 }
 
 // Gradient through the last layer into the fifth layer's pre-activation:
@@ -537,9 +603,13 @@ cnn_last_backward_kernel(const float* __restrict__ gy, const uint4* __restrict__
     const ActGeom G = act_geom(N);
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= G.plane) return;
-    const long long rel = r - kRecGuard;
-    const int py = rel >= 0 ? (int)(rel / G.W) - 1 : -2;
-    const int px = rel >= 0 ? (int)(rel - (long long)(py + 1) * G.W) - 1 : -2;
+    int py = -2, px = -2;                       // pixel of record r (32-bit: r < 2^31)
+    if (r >= kRecGuard) {
+        const unsigned u = (unsigned)(r - kRecGuard);
+        const unsigned yy = u / (unsigned)G.W;
+        py = (int)yy - 1;
+        px = (int)(u - yy * (unsigned)G.W) - 1;
+    }
     const long long ib = (long long)blockIdx.y * kPlanes * G.plane;
     uint4* dst = g + ib + r;
     if ((unsigned)py >= (unsigned)N || (unsigned)px >= (unsigned)N) {
@@ -755,11 +825,11 @@ cudaError_t forward(const float* params, const float* x, float* y, void* ws, int
         cnn_prep_weights_kernel<<<(kC * kC * kTaps + 255) / 256, 256, 0, st>>>(
             params + param_offset(k + 1), w.wf[k], w.wb[k]);
     const ActGeom G = act_geom(N);
-    const dim3 rg((unsigned)((G.plane + 255) / 256), batch);
-    const dim3 pg((N * N + 255) / 256, batch);
+    const dim3 fg((unsigned)((G.plane + 2 * kFirstStride - 1) / (2 * kFirstStride)), batch);
+    const dim3 lg((N / kLT) * (N / kLT), batch);
     // h1 .. h5 in act[0..4] when saving for the backward pass, else ping-pong in act[0..1]
     auto hbuf = [&](int k) { return save ? w.act[k] : w.act[k & 1]; };
-    cnn_first_kernel<<<rg, 256, 0, st>>>(x, params, hbuf(0), N);
+    cnn_first_kernel<<<fg, 128, 0, st>>>(x, params, hbuf(0), N);
     const int sms = device_sms();
     if (sms <= 0) return cudaErrorInvalidDevice;
     for (int k = 1; k <= 4; ++k) {
@@ -768,7 +838,7 @@ cudaError_t forward(const float* params, const float* x, float* y, void* ws, int
                                                                nullptr, hbuf(k), N, batch, sms, st);
         if (e != cudaSuccess) return e;
     }
-    cnn_last_kernel<<<pg, 256, 0, st>>>(x, hbuf(4), params + param_offset(5), y, N);
+    cnn_last_kernel<<<lg, kLT * kLT / 2, 0, st>>>(x, hbuf(4), params + param_offset(5), y, N);
     return cudaGetLastError();
 }
 

@@ -1174,4 +1174,19 @@ fbp_status fbp_last_device_error(fbp_plan_t p)
     return (fbp_status)v;
 }
 
+#ifdef FBP_BOUNDS_CHECK
+#include "../../include/fbp_check.h"
+
+fbp_status fbp_check_set_row_angle(fbp_plan_t p, int q, int i, int k0)
+{
+    if (!p || q < 0 || q >= 4 || i < 0 || i >= p->N) return FBP_ERR_INVALID_ARG;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return FBP_ERR_CUDA;
+    fbp::RowGeom* row = p->d_geom + (size_t)q * p->N + i;
+    return cudaMemcpy(&row->k0, &k0, sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess
+               ? FBP_OK : FBP_ERR_CUDA;
+}
+#endif
+
 }  // extern "C"

@@ -57,6 +57,52 @@ constexpr int kIirMaxWarps = 32;   // warps per row, so M <= 32 * 32 * 23
 }  // namespace fbp
 
 namespace fbp {
+// Device status word.  The pipeline's kernels validate the geometry table rows they use
+// (always) and, in a build with FBP_BOUNDS_CHECK defined, every global index they form and
+// the shared-memory range of every Hough round; a failed check records FBP_ERR_INTERNAL in
+// the plan's status word (the first code recorded wins), skips the access (a skipped load
+// reads 0, a rejected row is all zeros) and carries on.  fbp_last_device_error reads it.
+#ifdef FBP_BOUNDS_CHECK
+constexpr bool kBoundsCheck = true;
+#else
+constexpr bool kBoundsCheck = false;
+#endif
+
+__device__ __forceinline__ void flag_status(int* status, int code)
+{
+    if (status) atomicCAS(status, 0, code);
+}
+
+// 0 <= i < n; in the unchecked build always true (and compiled away).
+__device__ __forceinline__ bool in_bounds(int* status, long long i, long long n)
+{
+    if (!kBoundsCheck) return true;
+    if (i >= 0 && i < n) return true;
+    flag_status(status, (int)FBP_ERR_INTERNAL);
+    return false;
+}
+
+// A checked region of global memory: loads outside [base, base + n) read 0 and stores there
+// are dropped (checked build only; otherwise plain accesses).
+struct Span {
+    const float* base;
+    long long n;
+    int* status;
+    __device__ __forceinline__ bool ok(const float* p) const { return in_bounds(status, p - base, n); }
+};
+
+__device__ __forceinline__ float ldg_in(const Span& s, const float* p)
+{
+    return s.ok(p) ? __ldg(p) : 0.0f;
+}
+
+// A geometry row names angle rows inside the sinogram: k0 in [0, K), and the second angle
+// row k0 + 1 < K unless the row wraps (k0 = K - 1, second row = row 0 mirrored).
+__host__ __device__ inline bool row_geom_valid(const RowGeom& g, int K)
+{
+    return g.k0 >= 0 && g.k0 < K && (g.wrap == 0 ? g.k0 + 1 < K : (g.wrap == 1 && g.k0 == K - 1));
+}
+
 // Transposed resampling table.  Sinogram rows are taken kRsRows at a time; an entry is one
 // linogram row whose resampling reads rows of the group: code = 2 (q N + i) + mirrored
 // (1: the row-0 read past the last angle, detector mirrored), w[r] = its weight into group

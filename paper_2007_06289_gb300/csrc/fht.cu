@@ -80,6 +80,13 @@ __device__ __forceinline__ float ld_bin(const float* __restrict__ row, int M, in
     return (unsigned)j < (unsigned)M ? v : 0.0f;
 }
 
+__device__ __forceinline__ float ld_bin(const float* __restrict__ row, int M, int j, const Span& sp)
+{
+    const int jc = min(max(j, 0), M - 1);
+    const float v = ldg_in(sp, row + jc);
+    return (unsigned)j < (unsigned)M ? v : 0.0f;
+}
+
 __device__ __forceinline__ float row_lerp(const float* __restrict__ row, int M, int j, float f)
 {
     const float v0 = ld_bin(row, M, j);
@@ -110,10 +117,11 @@ __device__ __forceinline__ float linogram_sample(const RowGeom& g, const float* 
     return fmaf(g.w1, vb, g.w0 * va);
 }
 
-// Plain resampling into the stored linogram [count][4][N][2N] (every entry written).
+// Plain resampling into the stored linogram [count][4][N][2N] (every entry written; a
+// geometry row that fails validation resamples to zeros and sets the status word).
 __global__ void __launch_bounds__(256)
 resample_kernel(const float* __restrict__ filt, float* __restrict__ lin,
-                const RowGeom* __restrict__ geom, int N, int K, int M)
+                const RowGeom* __restrict__ geom, int N, int K, int M, int count, int* status)
 {
     const int W = 2 * N;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -121,8 +129,15 @@ resample_kernel(const float* __restrict__ filt, float* __restrict__ lin,
     const int s = blockIdx.z;
     if (c >= W) return;
     const RowGeom g = geom[qi];
+    const size_t o = ((size_t)s * 4 * N + qi) * W + c;
+    if (!in_bounds(status, (long long)o, (long long)count * 4 * N * W)) return;
+    if (!row_geom_valid(g, K)) {
+        if (c == 0) flag_status(status, (int)FBP_ERR_INTERNAL);
+        lin[o] = 0.0f;
+        return;
+    }
     const float* pt = filt + (size_t)s * K * M;
-    lin[((size_t)s * 4 * N + qi) * W + c] = linogram_sample(g, pt, M, g.b_fx + g.a_fx * (long long)c);
+    lin[o] = linogram_sample(g, pt, M, g.b_fx + g.a_fx * (long long)c);
 }
 
 // ------------------------------------------------------------------------ Hough rounds
@@ -153,10 +168,13 @@ __device__ __forceinline__ void st4(float* p, const float (&o)[4])
 
 // Stage 1 (shift 0) on row pairs (2m, 2m+1), in place, one warp per pair.
 template <int R, int WB, int PITCH, int NWARPS, class Sink>
-__device__ __forceinline__ void round_r2(float* buf, int warp, int lane, const Sink& sink)
+__device__ __forceinline__ void round_r2(float* buf, int warp, int lane, const Sink& sink,
+                                         int* status)
 {
     static_assert(WB % 128 == 0 && PITCH % 4 == 0, "chunked rows");
     for (int pr = warp; pr < R / 2; pr += NWARPS) {
+        // furthest float read: row 2pr+1, column (WB - 128) + 4 * 31 + 4
+        if (!in_bounds(status, (2 * pr + 1) * PITCH + WB + 0, (long long)R * PITCH)) continue;
         float* A = buf + (2 * pr) * PITCH + 4 * lane;
         float* B = A + PITCH;
         if constexpr (!std::is_same<Sink, SmemSink>::value) {
@@ -190,14 +208,18 @@ __device__ __forceinline__ void round_r2(float* buf, int warp, int lane, const S
 
 // Stages s and s+1 on the quad {a, a+h, a+2h, a+3h} whose first-stage shift is t = tb + T3
 // (tb a multiple of 4).  A..D point at column 4l of the four rows.
-template <int T3, int WB, class Sink>
+template <int T3, int WB, int R, int PITCH, class Sink>
 __device__ __forceinline__ void quad_r4(float* A, float* B, float* C, float* D, int tb, int a,
-                                        int h, int lane, const Sink& sink)
+                                        int h, int lane, const Sink& sink, int* status)
 {
     // 16-byte words holding rows B, C, D at columns 4l + t + k, 4l + 2t + k, 4l + 3t + k
     constexpr int cb = (2 * T3) & ~3, c3 = (2 * T3) & 3;
     constexpr int db = (3 * T3) & ~3, d3 = (3 * T3) & 3;
     constexpr bool d_three = d3 + 6 > 7;
+    // furthest float read: row a + 3h at 3 tb + db + (WB - 128) + 4 * 31 + (d_three ? 11 : 7)
+    if (!in_bounds(status, (long long)(a + 3 * h) * PITCH + 3 * tb + db + WB - 4 + (d_three ? 11 : 7),
+                   (long long)R * PITCH))
+        return;
     const float* Bw = B + tb;
     const float* Cw = C + 2 * tb + cb;
     const float* Dw = D + 3 * tb + db;
@@ -259,7 +281,8 @@ __device__ __forceinline__ void quad_r4(float* A, float* B, float* C, float* D, 
 
 // Stages s and s+1 (h = 2^(s-1)) on row quads, in place, one warp per quad.
 template <int R, int WB, int PITCH, int NWARPS, class Sink>
-__device__ __forceinline__ void round_r4(float* buf, int s, int warp, int lane, const Sink& sink)
+__device__ __forceinline__ void round_r4(float* buf, int s, int warp, int lane, const Sink& sink,
+                                         int* status)
 {
     static_assert(WB % 128 == 0 && PITCH % 4 == 0, "chunked rows");
     const int h = 1 << (s - 1);
@@ -273,10 +296,10 @@ __device__ __forceinline__ void round_r4(float* buf, int s, int warp, int lane, 
         float* D = A + 3 * h * PITCH;
         const int tb = t & ~3;
         switch (t & 3) {                                   // the same for the whole warp
-            case 0: quad_r4<0, WB>(A, B, C, D, tb, a, h, lane, sink); break;
-            case 1: quad_r4<1, WB>(A, B, C, D, tb, a, h, lane, sink); break;
-            case 2: quad_r4<2, WB>(A, B, C, D, tb, a, h, lane, sink); break;
-            default: quad_r4<3, WB>(A, B, C, D, tb, a, h, lane, sink); break;
+            case 0: quad_r4<0, WB, R, PITCH>(A, B, C, D, tb, a, h, lane, sink, status); break;
+            case 1: quad_r4<1, WB, R, PITCH>(A, B, C, D, tb, a, h, lane, sink, status); break;
+            case 2: quad_r4<2, WB, R, PITCH>(A, B, C, D, tb, a, h, lane, sink, status); break;
+            default: quad_r4<3, WB, R, PITCH>(A, B, C, D, tb, a, h, lane, sink, status); break;
         }
     }
 }
@@ -284,26 +307,27 @@ __device__ __forceinline__ void round_r4(float* buf, int s, int warp, int lane, 
 // All LOGR stages on the R = 2^LOGR rows of `buf`; row j holds slope rev(j).  The last
 // round hands its results to `sink` (SmemSink: back into `buf`).
 template <int LOGR, int WB, int PITCH, int NWARPS, class Sink>
-__device__ __forceinline__ void hough_stages(float* buf, int warp, int lane, const Sink& sink)
+__device__ __forceinline__ void hough_stages(float* buf, int warp, int lane, const Sink& sink,
+                                             int* status)
 {
     constexpr int R = 1 << LOGR;
     const SmemSink in_place;
     if constexpr (LOGR == 1) {
-        round_r2<R, WB, PITCH, NWARPS>(buf, warp, lane, sink);
+        round_r2<R, WB, PITCH, NWARPS>(buf, warp, lane, sink, status);
         __syncthreads();
     } else {
         int s = 1;
         if (LOGR & 1) {
-            round_r2<R, WB, PITCH, NWARPS>(buf, warp, lane, in_place);
+            round_r2<R, WB, PITCH, NWARPS>(buf, warp, lane, in_place, status);
             __syncthreads();
             s = 2;
         }
 #pragma unroll 1
         for (; s + 2 < LOGR; s += 2) {
-            round_r4<R, WB, PITCH, NWARPS>(buf, s, warp, lane, in_place);
+            round_r4<R, WB, PITCH, NWARPS>(buf, s, warp, lane, in_place, status);
             __syncthreads();
         }
-        round_r4<R, WB, PITCH, NWARPS>(buf, s, warp, lane, sink);
+        round_r4<R, WB, PITCH, NWARPS>(buf, s, warp, lane, sink, status);
         __syncthreads();
     }
 }
@@ -344,6 +368,7 @@ __device__ __forceinline__ int g_shift(int tau, int bi) { return (-tau * bi) & 3
 struct GShiftSink {
     float* rows;            // storage offset 0 of G row 0 of this (slice, quarter, block) tile
     int W, T, c0, N, bi, logr, lane;
+    Span g;                 // the whole G buffer (checked build: stores outside are dropped)
     mutable float carry[4][3];
     // per slot: the G row, its shift and the end of its stored offsets, set by begin()
     mutable float* dst[4];
@@ -380,11 +405,11 @@ struct GShiftSink {
             default: v[0] = p1; v[1] = p2; v[2] = p3; v[3] = o[0]; break;
         }
         if (x0 >= lo && x0 + 4 <= hi) {
-            st4(d, v);
+            if (g.ok(d) && g.ok(d + 3)) st4(d, v);
         } else {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if (x0 + k >= lo && x0 + k < hi) d[k] = v[k];
+                if (x0 + k >= lo && x0 + k < hi && g.ok(d + k)) d[k] = v[k];
         }
     }
 };
@@ -395,6 +420,8 @@ struct Pass1Args {
     float* g;               // [count][4][N][2N]
     const RowGeom* geom;
     int N, K, M, pitch;
+    long long src_n, g_n;   // floats of src and g (checked build)
+    int* status;
 };
 
 // One warp resamples one linogram row over a WB-column tile: lane l computes columns
@@ -408,7 +435,7 @@ struct Pass1Args {
 template <int WB, bool CLIP>
 __device__ __forceinline__ void resample_row(float* row, const float* ra, int pitch, int M,
                                              long long m, long long step, float w0, float w1,
-                                             int lim)
+                                             int lim, const Span& src)
 {
     constexpr int kS = 4;
 #pragma unroll
@@ -419,10 +446,10 @@ __device__ __forceinline__ void resample_row(float* row, const float* ra, int pi
             int j;
             split_fixed(m, j, fr[k]);
             const float* pp = ra + min(max(j, -kGuard), M);
-            l0[k] = __ldg(pp);
-            l1[k] = __ldg(pp + 1);
-            l2[k] = __ldg(pp + pitch);
-            l3[k] = __ldg(pp + pitch + 1);
+            l0[k] = ldg_in(src, pp);
+            l1[k] = ldg_in(src, pp + 1);
+            l2[k] = ldg_in(src, pp + pitch);
+            l3[k] = ldg_in(src, pp + pitch + 1);
         }
 #pragma unroll
         for (int k = 0; k < kS; ++k) {
@@ -474,6 +501,7 @@ pass1_kernel(Pass1Args a)
     if (c0 >= N + R * bi) return;                      // nothing needed in this tile
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const size_t lin_q = ((size_t)s * 4 + q) * N;      // row index base of this quarter
+    const Span src{a.src, a.src_n, a.status};
 
     if (FROM_LIN) {
         for (int idx = threadIdx.x; idx < R * WB; idx += kNT1) {
@@ -481,8 +509,9 @@ pass1_kernel(Pass1Args a)
             const int x = idx - j * WB;
             const int i = bi * R + j;
             const int c = c0 + x;
-            const bool ok = c <= N - 1 + i;
-            cp_async4(buf + j * PITCH + x, ok ? a.src + (lin_q + i) * W + c : a.src, ok);
+            const float* sp = a.src + (lin_q + i) * W + c;
+            const bool ok = c <= N - 1 + i && src.ok(sp);
+            cp_async4(buf + j * PITCH + x, ok ? sp : a.src, ok);
         }
     } else {
         // One warp per linogram row, lane = column within each 32-column group.  Rows of
@@ -499,7 +528,9 @@ pass1_kernel(Pass1Args a)
             const int j = warp * RPW + jj;
             if (j >= R) break;
             const int i = bi * R + j;
-            if (c0 <= N - 1 + i) prefetch_tile_row<WB>(pt, pitch, M, a.geom[q * N + i], c0, lane);
+            const RowGeom gm = a.geom[q * N + i];
+            if (c0 <= N - 1 + i && row_geom_valid(gm, a.K))
+                prefetch_tile_row<WB>(pt, pitch, M, gm, c0, lane);
         }
         for (int jj = 0; jj < RPW; ++jj) {
             const int j = warp * RPW + jj;
@@ -513,15 +544,21 @@ pass1_kernel(Pass1Args a)
                 continue;
             }
             const RowGeom gm = a.geom[q * N + i];
+            if (!row_geom_valid(gm, a.K)) {                   // rejected row: zeros
+                if (lane == 0 && blockIdx.x == 0) flag_status(a.status, (int)FBP_ERR_INTERNAL);
+#pragma unroll
+                for (int k = 0; k < WB / 32; ++k) row[32 * k] = 0.0f;
+                continue;
+            }
             const float* ra = pt + (size_t)gm.k0 * pitch;
             const long long m0 = gm.b_fx + gm.a_fx * (long long)(c0 + lane);
             const long long step = gm.a_fx * 32;
             if (!gm.wrap) {
                 if (c0 + WB - 1 <= limit)                      // whole tile inside the trapezoid
-                    resample_row<WB, false>(row, ra, pitch, M, m0, step, gm.w0, gm.w1, 0);
+                    resample_row<WB, false>(row, ra, pitch, M, m0, step, gm.w0, gm.w1, 0, src);
                 else
                     resample_row<WB, true>(row, ra, pitch, M, m0, step, gm.w0, gm.w1,
-                                           limit - c0 - lane);
+                                           limit - c0 - lane, src);
                 continue;
             }
             const float* rb = pt;                              // wrap: row 0, mirrored
@@ -536,10 +573,10 @@ pass1_kernel(Pass1Args a)
                     split_fixed(m, ja, fa[k]);
                     if (gm.wrap) split_fixed(mirror - m, jb, fb[k]);
                     else { jb = ja; fb[k] = fa[k]; }
-                    a0[k] = ld_bin(ra, M, ja);
-                    a1[k] = ld_bin(ra, M, ja + 1);
-                    b0[k] = ld_bin(rb, M, jb);
-                    b1[k] = ld_bin(rb, M, jb + 1);
+                    a0[k] = ld_bin(ra, M, ja, src);
+                    a1[k] = ld_bin(ra, M, ja + 1, src);
+                    b0[k] = ld_bin(rb, M, jb, src);
+                    b1[k] = ld_bin(rb, M, jb + 1, src);
                 }
 #pragma unroll
                 for (int k = 0; k < kS; ++k) {
@@ -556,8 +593,9 @@ pass1_kernel(Pass1Args a)
     if (FROM_LIN) cp_async_wait_all();
     __syncthreads();
 
-    const GShiftSink out{a.g + (lin_q + (size_t)bi * R) * W + c0, W, T, c0, N, bi, LOGR, lane, {}};
-    hough_stages<LOGR, WB, PITCH, NWARPS>(buf, warp, lane, out);
+    const GShiftSink out{a.g + (lin_q + (size_t)bi * R) * W + c0, W, T, c0, N, bi, LOGR, lane,
+                         Span{a.g, a.g_n, a.status}, {}};
+    hough_stages<LOGR, WB, PITCH, NWARPS>(buf, warp, lane, out, a.status);
 }
 
 // ------------------------------------------------------------------------ pass 2
@@ -566,6 +604,8 @@ struct Pass2Args {
     float* img;             // [count][N][N]
     float* const* img_tab;  // optional: slice s's image at img_tab[s]
     int N, n1;
+    long long g_n;          // floats of g (checked build)
+    int* status;
 };
 
 // 16-byte asynchronous copy; src_bytes = 0 writes zeros (src is then not read).
@@ -617,6 +657,8 @@ pass2_kernel(Pass2Args a)
     const int s = blockIdx.z;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* img = a.img_tab ? a.img_tab[s] : a.img + (size_t)s * N * N;
+    const Span gs{a.g, a.g_n, a.status};
+    const Span is{img, (long long)N * N, a.status};    // this slice's image
 
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
@@ -639,14 +681,14 @@ pass2_kernel(Pass2Args a)
 #pragma unroll
             for (int m = lane; m < WB / 4; m += 32) {
                 const int st = sb + 4 * m;
-                if (st >= lo && st + 4 <= hi) {
+                if (st >= lo && st + 4 <= hi && gs.ok(grow + st) && gs.ok(grow + st + 3)) {
                     cp_async16(drow + 4 * m, grow + st, 16);
                 } else if (st + 4 <= lo || st >= hi) {
                     cp_async16(drow + 4 * m, grow, 0);
                 } else {
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const bool ok = st + k >= lo && st + k < hi;
+                        const bool ok = st + k >= lo && st + k < hi && gs.ok(grow + st + k);
                         cp_async4(drow + 4 * m + k, ok ? grow + st + k : grow, ok);
                     }
                 }
@@ -657,10 +699,10 @@ pass2_kernel(Pass2Args a)
     }
     cp_async_wait_group<1>();
     __syncthreads();
-    hough_stages<LOGR2, WB, PITCH, NWARPS>(hb0, warp, lane, SmemSink{});
+    hough_stages<LOGR2, WB, PITCH, NWARPS>(hb0, warp, lane, SmemSink{}, a.status);
     cp_async_wait_group<0>();
     __syncthreads();
-    hough_stages<LOGR2, WB, PITCH, NWARPS>(hb1, warp, lane, SmemSink{});
+    hough_stages<LOGR2, WB, PITCH, NWARPS>(hb1, warp, lane, SmemSink{}, a.status);
 
     // F_- + F_+ for slot row j (slope tau_lo = rev(j)) at intercept x0 + xx: columns xx of
     // hb0 and T2-1-xx of hb1, taken as 16-byte words (the second one reversed).
@@ -675,7 +717,7 @@ pass2_kernel(Pass2Args a)
                 ld4(vb, r1 + T2 - 4 - xx);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) o[k] = va[k] + vb[3 - k];
-                st4(out + xx, o);
+                if (is.ok(out + xx) && is.ok(out + xx + 3)) st4(out + xx, o);
             }
         }
     } else {
@@ -710,10 +752,12 @@ pass2_kernel(Pass2Args a)
                 float v[kB];
 #pragma unroll
                 for (int u = 0; u < kB; ++u)
-                    if (xb + NWARPS * u < nx) v[u] = out[(size_t)NWARPS * u * N];
+                    if (xb + NWARPS * u < nx && is.ok(out + (size_t)NWARPS * u * N))
+                        v[u] = out[(size_t)NWARPS * u * N];
 #pragma unroll
                 for (int u = 0; u < kB; ++u)
-                    if (xb + NWARPS * u < nx) out[(size_t)NWARPS * u * N] = v[u] + src[NWARPS * u * TP];
+                    if (xb + NWARPS * u < nx && is.ok(out + (size_t)NWARPS * u * N))
+                        out[(size_t)NWARPS * u * N] = v[u] + src[NWARPS * u * TP];
             }
         }
     }
@@ -721,7 +765,8 @@ pass2_kernel(Pass2Args a)
 
 // Single-pass sizes (n <= 6): G already holds the quarter images H_q[tau][u]; sum them.
 __global__ void __launch_bounds__(256)
-combine_kernel(const float* __restrict__ g, float* __restrict__ img, float* const* img_tab, int N)
+combine_kernel(const float* __restrict__ g, float* __restrict__ img, float* const* img_tab, int N,
+               long long g_n, int* status)
 {
     const int W = 2 * N;
     const int s = blockIdx.y;
@@ -731,8 +776,9 @@ combine_kernel(const float* __restrict__ g, float* __restrict__ img, float* cons
     const int x = p - y * N;
     const float* h = g + (size_t)s * 4 * N * W;
     const size_t qs = (size_t)N * W;
-    const float v = h[(size_t)y * W + x] + h[qs + (size_t)y * W + (N - 1 - x)];
-    const float hh = h[2 * qs + (size_t)x * W + y] + h[3 * qs + (size_t)x * W + (N - 1 - y)];
+    const Span gs{g, g_n, status};
+    const float v = ldg_in(gs, h + (size_t)y * W + x) + ldg_in(gs, h + qs + (size_t)y * W + (N - 1 - x));
+    const float hh = ldg_in(gs, h + 2 * qs + (size_t)x * W + y) + ldg_in(gs, h + 3 * qs + (size_t)x * W + (N - 1 - y));
     (img_tab ? img_tab[s] : img + (size_t)s * N * N)[p] = v + hh;
 }
 
@@ -743,6 +789,14 @@ constexpr size_t pass1_smem() { return (size_t)(1 << LOGR) * hough_pitch<(1 << L
 template <int LOGR2, int T2>
 constexpr size_t pass2_smem() { return (size_t)pass2_floats<LOGR2, T2>() * sizeof(float); }
 
+// floats of pass 1's input: a stored linogram, or the guarded filtered sinograms
+template <bool FROM_LIN>
+long long from_lin_floats(const fbp_plan_s* p, int count)
+{
+    return FROM_LIN ? (long long)count * (long long)lin_floats(p)
+                    : (long long)count * p->K * filt_pitch(p);
+}
+
 template <int LOGR, bool FROM_LIN>
 cudaError_t launch_pass1_t(const fbp_plan_s* p, const float* src, float* g, int count,
                            cudaStream_t st)
@@ -752,7 +806,9 @@ cudaError_t launch_pass1_t(const fbp_plan_s* p, const float* src, float* g, int 
     const int nblocks = p->N >> LOGR;
     const int max_cols = p->N + R * (nblocks - 1);
     dim3 grid((max_cols + T - 1) / T, 4 * nblocks, count);
-    Pass1Args a{src, g, p->d_geom, p->N, p->K, p->M, filt_pitch(p)};
+    const long long src_n = from_lin_floats<FROM_LIN>(p, count);
+    Pass1Args a{src, g, p->d_geom, p->N, p->K, p->M, filt_pitch(p), src_n,
+                (long long)count * (long long)lin_floats(p), p->d_status};
     pass1_kernel<LOGR, FROM_LIN><<<grid, kNT1, pass1_smem<LOGR>(), st>>>(a);
     return cudaGetLastError();
 }
@@ -762,7 +818,8 @@ cudaError_t launch_pass2_t(const fbp_plan_s* p, const float* g, float* img, int 
                            cudaStream_t st, float* const* img_tab)
 {
     dim3 grid((p->N + T2 - 1) / T2, p->N >> LOGR2, count);
-    Pass2Args a{g, img, img_tab, p->N, p->n1};
+    Pass2Args a{g, img, img_tab, p->N, p->n1, (long long)count * (long long)lin_floats(p),
+                p->d_status};
     pass2_kernel<LOGR2, T2, HORIZ><<<grid, kNT2, pass2_smem<LOGR2, T2>(), st>>>(a);
     return cudaGetLastError();
 }
@@ -816,7 +873,8 @@ cudaError_t launch_resample(const fbp_plan_s* p, const float* filt, float* lin, 
 {
     if (count <= 0) return cudaSuccess;
     dim3 grid((2 * p->N + 255) / 256, 4 * p->N, count);
-    resample_kernel<<<grid, 256, 0, st>>>(filt, lin, p->d_geom, p->N, p->K, p->M);
+    resample_kernel<<<grid, 256, 0, st>>>(filt, lin, p->d_geom, p->N, p->K, p->M, count,
+                                          p->d_status);
     return cudaGetLastError();
 }
 
@@ -841,7 +899,8 @@ cudaError_t launch_pass2(const fbp_plan_s* p, const float* g, float* img, int co
     if (p->n2 == 0) {
         if (horizontal) return cudaSuccess;            // the sum kernel does all quarters
         dim3 grid((p->N * p->N + 255) / 256, count);
-        combine_kernel<<<grid, 256, 0, st>>>(g, img, img_tab, p->N);
+        combine_kernel<<<grid, 256, 0, st>>>(g, img, img_tab, p->N,
+                                             (long long)count * (long long)lin_floats(p), p->d_status);
         return cudaGetLastError();
     }
     switch (p->n2 * 2 + (horizontal ? 1 : 0)) {

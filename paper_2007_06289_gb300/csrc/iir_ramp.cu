@@ -255,29 +255,40 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
 
+// gs: the global buffer the row lies in (checked build: copies outside it are skipped)
 __device__ __forceinline__ void load_row(float* dst, const float* src, long long e0, int M,
-                                         int t, int nthr)
+                                         int t, int nthr, const Span& gs)
 {
     const int h = min((int)((4 - (e0 & 3)) & 3), M);
     const int groups = (M - h) >> 2;
-    for (int g = t; g < groups; g += nthr) cp_async16(dst + h + 4 * g, src + h + 4 * g);
+    for (int g = t; g < groups; g += nthr)
+        if (gs.ok(src + h + 4 * g) && gs.ok(src + h + 4 * g + 3))
+            cp_async16(dst + h + 4 * g, src + h + 4 * g);
     const int tail0 = h + 4 * groups;
-    if (t < h) cp_async4(dst + t, src + t);
-    if (t < M - tail0) cp_async4(dst + tail0 + t, src + tail0 + t);
+    if (t < h && gs.ok(src + t)) cp_async4(dst + t, src + t);
+    if (t < M - tail0 && gs.ok(src + tail0 + t)) cp_async4(dst + tail0 + t, src + tail0 + t);
 }
 
 __device__ __forceinline__ void store_row(float* dst, const float* src, long long e0, int M,
-                                          int t, int nthr)
+                                          int t, int nthr, const Span& gs)
 {
     const int h = min((int)((4 - (e0 & 3)) & 3), M);
     const int groups = (M - h) >> 2;
     const float4* s4 = reinterpret_cast<const float4*>(src + h);
     float4* d4 = reinterpret_cast<float4*>(dst + h);
-    for (int g = t; g < groups; g += nthr) d4[g] = s4[g];
+    for (int g = t; g < groups; g += nthr)
+        if (gs.ok(dst + h + 4 * g) && gs.ok(dst + h + 4 * g + 3)) d4[g] = s4[g];
     const int tail0 = h + 4 * groups;
-    if (t < h) dst[t] = src[t];
-    if (t < M - tail0) dst[tail0 + t] = src[tail0 + t];
+    if (t < h && gs.ok(dst + t)) dst[t] = src[t];
+    if (t < M - tail0 && gs.ok(dst + tail0 + t)) dst[tail0 + t] = src[tail0 + t];
 }
+
+// Input and output extents and the status word, for the checked build.
+struct IirIo {
+    long long in_n;          // floats of `in` (or of one slice table entry, K M)
+    long long out_n;         // floats of `out`
+    int* status;
+};
 
 // LT > 0: every lane filters exactly LT samples (the plan's L), loops fully unrolled; LT = 0:
 // runtime L.  Lanes past the end of the row filter the zero padding of the shared row.
@@ -285,7 +296,7 @@ __device__ __forceinline__ void store_row(float* dst, const float* src, long lon
 template <int JR, int JC, bool TAPS, int LT>
 __global__ void __launch_bounds__(kIirThreads)
 iir_ramp_kernel(const float* in, const float* const* in_tab, int K, float* out, int rows, int M,
-                int out_pitch, int rows_per_cta, IirParams prm)
+                int out_pitch, int rows_per_cta, IirParams prm, IirIo io)
 {
     constexpr int SF = state_floats<JR, JC>();
     extern __shared__ __align__(16) float smem[];
@@ -319,7 +330,7 @@ iir_ramp_kernel(const float* in, const float* const* in_tab, int K, float* out, 
     const int span = nthr * L;
 
     if (live) {
-        load_row(sp, in_base + e_in, e_in, M, t, nthr);
+        load_row(sp, in_base + e_in, e_in, M, t, nthr, Span{in_base, io.in_n, io.status});
         for (int n = M + t; n <= span; n += nthr) sp[n] = 0.0f;
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -397,9 +408,10 @@ iir_ramp_kernel(const float* in, const float* const* in_tab, int K, float* out, 
 
     if (live) {
         float* dst = out + e_out;
-        if (t < lead) dst[t - lead] = 0.0f;
-        if (t < out_pitch - M - lead) dst[M + t] = 0.0f;
-        store_row(dst, sz, e_out, M, t, nthr);
+        const Span os{out, io.out_n, io.status};
+        if (t < lead && os.ok(dst + t - lead)) dst[t - lead] = 0.0f;
+        if (t < out_pitch - M - lead && os.ok(dst + M + t)) dst[M + t] = 0.0f;
+        store_row(dst, sz, e_out, M, t, nthr, os);
     }
 }
 
@@ -414,7 +426,7 @@ iir_ramp_kernel(const float* in, const float* const* in_tab, int K, float* out, 
 template <int JR, int JC>
 __global__ void __launch_bounds__(kIirThreads, 4)
 iir_ramp_regs_kernel(const float* in, const float* const* in_tab, int K, float* out, int rows,
-                     int M, int out_pitch, int rows_per_cta, IirParams prm)
+                     int M, int out_pitch, int rows_per_cta, IirParams prm, IirIo io)
 {
     constexpr int L = kIirLmax;
     constexpr int SF = state_floats<JR, JC>();
@@ -444,7 +456,7 @@ iir_ramp_regs_kernel(const float* in, const float* const* in_tab, int K, float* 
     const int span = nthr * L;
 
     if (live) {
-        load_row(sp, in_base + e_in, e_in, M, t, nthr);
+        load_row(sp, in_base + e_in, e_in, M, t, nthr, Span{in_base, io.in_n, io.status});
         for (int n = M + t; n <= span; n += nthr) sp[n] = 0.0f;
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -494,9 +506,10 @@ iir_ramp_regs_kernel(const float* in, const float* const* in_tab, int K, float* 
 
     if (live) {
         float* dst = out + e_out;
-        if (t < lead) dst[t - lead] = 0.0f;
-        if (t < out_pitch - M - lead) dst[M + t] = 0.0f;
-        store_row(dst, sz, e_out, M, t, nthr);
+        const Span os{out, io.out_n, io.status};
+        if (t < lead && os.ok(dst + t - lead)) dst[t - lead] = 0.0f;
+        if (t < out_pitch - M - lead && os.ok(dst + M + t)) dst[M + t] = 0.0f;
+        store_row(dst, sz, e_out, M, t, nthr, os);
     }
 }
 
@@ -512,15 +525,17 @@ cudaError_t launch_iir_t(const fbp_plan_s* p, const float* in, float* out, int r
     const size_t smem = ((size_t)rows_per_cta * 2 * rb + (size_t)rows_per_cta * 2 * wpr * SF) * sizeof(float);
     if (smem > (size_t)kMaxSmem || threads > 1024) return cudaErrorInvalidValue;
     const int grid = (rows + rows_per_cta - 1) / rows_per_cta;
+    const IirIo io{in_tab ? (long long)p->K * p->M : (long long)rows * p->M,
+                   (long long)rows * out_pitch, p->d_status};
     if constexpr (!TAPS && LT == kIirLmax) {
         if (p->iir.diff) {
             iir_ramp_regs_kernel<JR, JC><<<grid, threads, smem, st>>>(
-                in, in_tab, p->K, out, rows, p->M, out_pitch, rows_per_cta, p->iir);
+                in, in_tab, p->K, out, rows, p->M, out_pitch, rows_per_cta, p->iir, io);
             return cudaGetLastError();
         }
     }
     iir_ramp_kernel<JR, JC, TAPS, LT><<<grid, threads, smem, st>>>(
-        in, in_tab, p->K, out, rows, p->M, out_pitch, rows_per_cta, p->iir);
+        in, in_tab, p->K, out, rows, p->M, out_pitch, rows_per_cta, p->iir, io);
     return cudaGetLastError();
 }
 

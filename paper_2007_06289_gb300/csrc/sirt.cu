@@ -27,7 +27,7 @@ __device__ __forceinline__ float bin_or_zero(const float* row, int M, int j)
 __global__ void __launch_bounds__(kSirtThreads)
 hough_data_kernel(const float* __restrict__ sino, float* __restrict__ lin,
                   const RowGeom* __restrict__ geom, const float2* __restrict__ hw, int N, int K,
-                  int M)
+                  int M, int* status)
 {
     const int W = 2 * N;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -35,6 +35,11 @@ hough_data_kernel(const float* __restrict__ sino, float* __restrict__ lin,
     const int s = blockIdx.z;
     if (c >= W) return;
     const RowGeom gm = geom[qi];
+    if (!row_geom_valid(gm, K)) {               // rejected geometry row: zeros
+        if (c == 0) flag_status(status, (int)FBP_ERR_INTERNAL);
+        lin[((size_t)s * 4 * N + qi) * W + c] = 0.0f;
+        return;
+    }
     const float2 w = hw[qi];
     const float* ps = sino + (size_t)s * K * M;
     const long long m = gm.b_fx + gm.a_fx * (long long)c;
@@ -130,7 +135,7 @@ cudaError_t launch_hough_data(const fbp_plan_s* p, const float* sino, float* lin
     if (count <= 0) return cudaSuccess;
     const dim3 grid((2 * p->N + kSirtThreads - 1) / kSirtThreads, 4 * p->N, count);
     hough_data_kernel<<<grid, kSirtThreads, 0, st>>>(sino, lin, p->d_geom, p->d_hough_w, p->N,
-                                                     p->K, p->M);
+                                                     p->K, p->M, p->d_status);
     return cudaGetLastError();
 }
 

@@ -86,3 +86,16 @@ def test_volume_arguments_are_checked_before_cuda(fbp):
     assert lib.fbp_volume_info(None, None, None) == 1
     assert lib.fbp_volume_group(None, 0, None, None, None, None, None, None) == 1
     assert lib.fbp_volume_destroy(None) == 0
+
+
+def test_checked_library_exports_the_abi_and_its_test_hook(fbp):
+    # the bounds-checked build: every function of include/fbp.h plus include/fbp_check.h;
+    # the ordinary library does not export the test hook
+    from paper_2007_06289_gb300 import build
+    path = build.build(bounds_check=True)
+    checked = ctypes.CDLL(path)
+    hooks = fbp.header_functions(fbp.CHECK_HEADER)
+    assert hooks == ["fbp_check_set_row_angle"]
+    for name in fbp.header_functions() + hooks:
+        assert hasattr(checked, name), name
+    assert not hasattr(fbp.load_library(), "fbp_check_set_row_angle")
