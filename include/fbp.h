@@ -115,6 +115,13 @@ fbp_status fbp_set_workspace(fbp_plan_t plan, void* d_ws, size_t bytes);
  * the same buffer. */
 fbp_status fbp_filter_iir(fbp_plan_t plan, const float* d_sino, float* d_filt, void* stream);
 
+/* Eq. 8 with L0 = M-1: the exact (non-recursive) ramp filter of every projection row,
+ * p~(n) = sum_{|k| <= M-1} h(k) p(n-k), h of Eq. 7 -- the filter of the direct FBP
+ * comparator, exposed so that the fast back projection can be run on exactly filtered data
+ * (which separates the recursive filter's share of the error from the dyadic lines').
+ * d_sino [batch][K][M] -> d_filt [batch][K][M] (distinct buffers).  Theta(K M^2). */
+fbp_status fbp_filter_fir(fbp_plan_t plan, const float* d_sino, float* d_filt, void* stream);
+
 /* Sec. 4.1-4.2, Eq. 14-15: bilinear resampling of the filtered sinogram into the four
  * weighted linogram quarters.  d_filt [batch][K][M] -> d_lin [batch][4][N][2N]; every
  * entry of d_lin is written. */

@@ -65,6 +65,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "fbp_set_workspace": (I, [P, V, S]),
         "fbp_set_chunk": (I, [P, I]),
         "fbp_filter_iir": (I, [P, V, V, V]),
+        "fbp_filter_fir": (I, [P, V, V, V]),
         "fbp_resample_st": (I, [P, V, V, V]),
         "fbp_fht_backproject": (I, [P, V, V, V]),
         "fbp_reconstruct": (I, [P, V, V, V]),
@@ -255,6 +256,12 @@ def fbp_filter_iir(plan: Plan, sino, filt, stream=None) -> None:
     _check("fbp_filter_iir", load_library().fbp_filter_iir(
         plan.handle, _dev_ptr(sino, plan.sino_shape, "sino"),
         _dev_ptr(filt, plan.sino_shape, "filt"), _stream_ptr(stream)))
+
+
+def fbp_filter_fir(plan: Plan, sino, filt, stream=None) -> None:
+    _check("fbp_filter_fir", load_library().fbp_filter_fir(
+        plan.handle, _dev_ptr(sino, plan.sino_shape, "sino"), _dev_ptr(filt, plan.sino_shape, "filt"),
+        _stream_ptr(stream)))
 
 
 def fbp_resample_st(plan: Plan, filt, lin, stream=None) -> None:

@@ -35,44 +35,80 @@ fir_ramp_kernel(const float* __restrict__ in, float* __restrict__ out, int M)
     }
 }
 
-constexpr int kBpTile = 16;
-constexpr int kBpTrig = 256;
+// Pixel-driven back projection.  CTA = 32 x 32 pixels, 256 threads, each thread 4 pixels of
+// one column (rows ty, ty + 8, ty + 16, ty + 24).  Angles go in blocks of kBpA: for each
+// angle of a block the detector window the tile reads (at most 31 (|cos| + |sin|) + 2 <= 46
+// bins wide, staged as kBpW bins from one below the lowest position) is copied into shared
+// memory with zeros outside [0, M), so the inner loop reads shared memory only.  Every
+// pixel's sum runs over the angles in order with the arithmetic of the plain per-pixel form.
+constexpr int kBpT = 32;
+constexpr int kBpRows = 4;                       // pixels per thread
+constexpr int kBpThreads = kBpT * kBpT / kBpRows;
+constexpr int kBpA = 32;                         // angles per staged block
+constexpr int kBpW = 64;                         // staged bins per angle
 
-// Pixel-driven back projection: one thread per pixel, angles streamed through a shared
-// table of (cos, sin).
-__global__ void __launch_bounds__(kBpTile * kBpTile)
+__global__ void __launch_bounds__(kBpThreads)
 direct_bp_kernel(const float* __restrict__ filt, float* __restrict__ img,
                  const float2* __restrict__ trig, int N, int K, int M)
 {
-    __shared__ float2 st[kBpTrig];
-    const int x = blockIdx.x * kBpTile + threadIdx.x;
-    const int y = blockIdx.y * kBpTile + threadIdx.y;
+    __shared__ float win[kBpA][kBpW];
+    __shared__ float2 scs[kBpA];
+    __shared__ int sjb[kBpA];
+    const int tid = threadIdx.x;
+    const int tx = tid % kBpT, ty = tid / kBpT;
+    const int xb = blockIdx.x * kBpT, yb = blockIdx.y * kBpT;
     const int s = blockIdx.z;
-    const int tid = threadIdx.y * kBpTile + threadIdx.x;
     const float c0 = 0.5f * (float)(N - 1);
-    const float xc = (float)x - c0;
-    const float yc = (float)y - c0;
     const float half = 0.5f * (float)(M - 1);
+    const float xc = (float)(xb + tx) - c0;
+    float yc[kBpRows], acc[kBpRows];
+#pragma unroll
+    for (int r = 0; r < kBpRows; ++r) {
+        yc[r] = (float)(yb + ty + (kBpT / kBpRows) * r) - c0;
+        acc[r] = 0.0f;
+    }
     const float* pt = filt + (size_t)s * K * M;
-    float acc = 0.0f;
-    for (int k0 = 0; k0 < K; k0 += kBpTrig) {
+    for (int k0 = 0; k0 < K; k0 += kBpA) {
+        const int ka = min(kBpA, K - k0);
+        __syncthreads();                                 // previous block consumed
+        if (tid < ka) {
+            const float2 cs = trig[k0 + tid];
+            // lowest detector position over the tile's corners, one bin of slack below
+            const float xl = (float)xb - c0, xh = xl + (float)(kBpT - 1);
+            const float yl = (float)yb - c0, yh = yl + (float)(kBpT - 1);
+            const float mlo = fminf(fminf(fmaf(xl, cs.x, fmaf(yl, cs.y, half)), fmaf(xh, cs.x, fmaf(yl, cs.y, half))),
+                                    fminf(fmaf(xl, cs.x, fmaf(yh, cs.y, half)), fmaf(xh, cs.x, fmaf(yh, cs.y, half))));
+            scs[tid] = cs;
+            sjb[tid] = (int)floorf(mlo) - 1;
+        }
         __syncthreads();
-        if (k0 + tid < K && tid < kBpTrig) st[tid] = trig[k0 + tid];
+        for (int e = tid; e < ka * kBpW; e += kBpThreads) {
+            const int a = e / kBpW, b = e - a * kBpW;
+            const int j = sjb[a] + b;
+            win[a][b] = (j >= 0 && j < M) ? __ldg(pt + (size_t)(k0 + a) * M + j) : 0.0f;
+        }
         __syncthreads();
-        const int kn = min(kBpTrig, K - k0);
-        for (int kk = 0; kk < kn; ++kk) {
-            const float2 cs = st[kk];
-            const float m = fmaf(xc, cs.x, fmaf(yc, cs.y, half));
-            const float fl = floorf(m);
-            const int j = (int)fl;
-            const float f = m - fl;
-            const float* row = pt + (size_t)(k0 + kk) * M;
-            const float v0 = (j >= 0 && j < M) ? __ldg(row + j) : 0.0f;
-            const float v1 = (j + 1 >= 0 && j + 1 < M) ? __ldg(row + j + 1) : 0.0f;
-            acc += fmaf(f, v1 - v0, v0);
+        for (int a = 0; a < ka; ++a) {
+            const float2 cs = scs[a];
+            const int jb = sjb[a];
+            const float* wr = win[a];
+#pragma unroll
+            for (int r = 0; r < kBpRows; ++r) {
+                const float m = fmaf(xc, cs.x, fmaf(yc[r], cs.y, half));
+                const float fl = floorf(m);
+                const int jl = min(max((int)fl - jb, 0), kBpW - 2);
+                const float f = m - fl;
+                const float v0 = wr[jl], v1 = wr[jl + 1];
+                acc[r] += fmaf(f, v1 - v0, v0);
+            }
         }
     }
-    if (x < N && y < N) img[((size_t)s * N + y) * N + x] = acc * (3.14159265358979323846f / (float)K);
+    const int x = xb + tx;
+#pragma unroll
+    for (int r = 0; r < kBpRows; ++r) {
+        const int y = yb + ty + (kBpT / kBpRows) * r;
+        if (x < N && y < N) img[((size_t)s * N + y) * N + x] = acc[r] * (3.14159265358979323846f / (float)K);
+    }
 }
 
 }  // namespace
@@ -96,9 +132,8 @@ cudaError_t launch_direct_bp(const fbp_plan_s* p, const float* filt, float* img,
                              cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    dim3 block(kBpTile, kBpTile);
-    dim3 grid((p->N + kBpTile - 1) / kBpTile, (p->N + kBpTile - 1) / kBpTile, count);
-    direct_bp_kernel<<<grid, block, 0, st>>>(filt, img, p->d_trig, p->N, p->K, p->M);
+    dim3 grid((p->N + kBpT - 1) / kBpT, (p->N + kBpT - 1) / kBpT, count);
+    direct_bp_kernel<<<grid, kBpThreads, 0, st>>>(filt, img, p->d_trig, p->N, p->K, p->M);
     return cudaGetLastError();
 }
 

@@ -782,6 +782,18 @@ fbp_status fbp_filter_iir(fbp_plan_t p, const float* d_sino, float* d_filt, void
     }));
 }
 
+fbp_status fbp_filter_fir(fbp_plan_t p, const float* d_sino, float* d_filt, void* stream)
+{
+    if (!p || !d_sino || !d_filt || d_sino == d_filt) return FBP_ERR_INVALID_ARG;
+    if (!aligned16(d_sino) || !aligned16(d_filt)) return FBP_ERR_MISALIGNED;
+    DeviceGuard g(p->device);
+    if (!g.ok) return FBP_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    return cuda_status(run(p, FBP_KERNEL_FIR, st, [&] {
+        return fbp::launch_fir(p, d_sino, d_filt, p->batch * p->K, st);
+    }));
+}
+
 fbp_status fbp_resample_st(fbp_plan_t p, const float* d_filt, float* d_lin, void* stream)
 {
     if (!p || !d_filt || !d_lin) return FBP_ERR_INVALID_ARG;

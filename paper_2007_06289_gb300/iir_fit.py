@@ -27,7 +27,10 @@ fitting length open.  This module fixes them as follows:
 Running this file rewrites the committed table ``iir_coeffs.json`` and the C include
 ``csrc/iir_table.inc`` that the library compiles in as its built-in coefficients;
 ``--windows`` rewrites ``iir_windows.json``, order-3 fits of the apodised ramps (Shepp-Logan,
-cosine, Hamming, Hann) that callers pass to fbp_plan as explicit coefficients.
+cosine, Hamming, Hann) that callers pass to fbp_plan as explicit coefficients; ``--mse``
+rewrites ``iir_coeffs_mse.json``, order-3 fits under the paper's own objective, the plain
+mean-square error of the impulse response: by Parseval the mean of (H(w) - w)^2 over a
+uniform grid on (0, 1/2], with the same constraints and search (``mse_coefficients``).
 """
 from __future__ import annotations
 
@@ -99,28 +102,40 @@ def window(w, name: str = "ram-lak") -> np.ndarray:
     raise ValueError(f"unknown window {name!r}")
 
 
-def best_b(a, Mb, w, target=None):
+def best_b(a, Mb, w, target=None, relative=True):
     """Least-squares b with sum(b) = 0 for the given feedback coefficients, matching H(w)/w
-    to `target` (the window; 1 for the plain ramp); returns (b, loss)."""
+    to `target` (the window; 1 for the plain ramp); returns (b, loss).  relative=False
+    matches H(w) to w target(w) instead (an unweighted response error)."""
     target = np.ones_like(w) if target is None else target
     Phi = _basis(a, Mb, w)
-    D = (Phi[:, :-1] - Phi[:, -1:]) / w[:, None]
-    bp, *_ = np.linalg.lstsq(D, target, rcond=None)
+    scale = w[:, None] if relative else np.ones_like(w)[:, None]
+    want = target if relative else w * target
+    D = (Phi[:, :-1] - Phi[:, -1:]) / scale
+    bp, *_ = np.linalg.lstsq(D, want, rcond=None)
     b = np.concatenate([bp, [-bp.sum()]])
-    r = Phi @ b / w - target
+    r = (Phi @ b) / scale[:, 0] - want
     return b, float(np.mean(r * r))
 
 
-def fit_coefficients(M: int, order: int, starts: int = 6, seed: int = 7, window_name="ram-lak"):
-    """Fit Q = Mb = order for a detector of M bins.  Returns (b, a, loss)."""
+def fit_coefficients(M: int, order: int, starts: int = 6, seed: int = 7, window_name="ram-lak",
+                     objective: str = "log"):
+    """Fit Q = Mb = order for a detector of M bins.  Returns (b, a, loss).
+    objective "log": (H(w)/w - 1)^2 on a log-spaced grid (the default table); "impulse":
+    (H(w) - w)^2 on a uniform grid, i.e. the impulse-response mean-square error."""
     from scipy.optimize import minimize
-    w = np.geomspace(1.0 / (4 * M), 0.5, 512)
+    relative = objective == "log"
+    if relative:
+        w = np.geomspace(1.0 / (4 * M), 0.5, 512)
+    elif objective == "impulse":
+        w = (np.arange(2 * M) + 0.5) / (4.0 * M)          # uniform on (0, 1/2)
+    else:
+        raise ValueError(objective)
     target = window(w, window_name)
 
     def loss(x):
         a = reflection_to_poly(KMAX * np.tanh(x))
         excess = np.abs(np.roots(np.concatenate([[1.0], a]))).max() - PMAX
-        return best_b(a, order, w, target)[1] + (1e3 * excess if excess > 0 else 0.0)
+        return best_b(a, order, w, target, relative)[1] + (1e3 * excess if excess > 0 else 0.0)
 
     rng = np.random.default_rng(seed)
     best = None
@@ -142,7 +157,7 @@ def fit_coefficients(M: int, order: int, starts: int = 6, seed: int = 7, window_
         if best is None or res.fun < best.fun:
             best = res
     a = reflection_to_poly(KMAX * np.tanh(best.x))
-    b, f = best_b(a, order, w, target)
+    b, f = best_b(a, order, w, target, relative)
     return b, a, f
 
 
@@ -206,6 +221,32 @@ def fit_windows():
                        entries=entries), fh, indent=1)
 
 
+def mse_coefficients(N: int, order: int = DEFAULT_ORDER):
+    """(b, a) of the committed impulse-response-MSE table (iir_coeffs_mse.json)."""
+    with open(os.path.join(_HERE, "iir_coeffs_mse.json")) as fh:
+        table = json.load(fh)
+    for e in table["entries"]:
+        if e["N"] == N and e["order"] == order:
+            return np.array(e["b"]), np.array(e["a"])
+    raise KeyError((N, order))
+
+
+def _fit_mse_entry(N):
+    M = detector_bins(N)
+    b, a, f = fit_coefficients(M, DEFAULT_ORDER, objective="impulse")
+    return dict(N=N, order=DEFAULT_ORDER, M=M, loss=f, b=list(map(float, b)), a=list(map(float, a)))
+
+
+def fit_mse():
+    """Rewrite iir_coeffs_mse.json: order-3 impulse-response MSE fits for WINDOW_SIZES."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(len(WINDOW_SIZES), os.cpu_count() or 1)) as pool:
+        entries = pool.map(_fit_mse_entry, WINDOW_SIZES)
+    with open(os.path.join(_HERE, "iir_coeffs_mse.json"), "w") as fh:
+        json.dump(dict(loss="mean (H(w) - w)^2, w uniform on (0, 1/2): the impulse-response MSE",
+                       entries=entries), fh, indent=1)
+
+
 def _fit_entry(job):
     N, order = job
     M = detector_bins(N)
@@ -235,5 +276,7 @@ def main(argv):
 if __name__ == "__main__":
     if sys.argv[1:2] == ["--windows"]:
         fit_windows()
+    elif sys.argv[1:2] == ["--mse"]:
+        fit_mse()
     else:
         main(sys.argv)

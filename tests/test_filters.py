@@ -77,3 +77,40 @@ def test_committed_window_fits():
         wm = w[::64]
         dtft = 2 * (g[None, :] * np.exp(-2j * np.pi * wm[:, None] * n[None, :])).sum(axis=1).real
         np.testing.assert_allclose(dtft, response(b, a, wm), rtol=0, atol=1e-6)
+
+
+def _response(b, a, w):
+    z = np.exp(-2j * np.pi * w)
+    num = sum(bk * z ** k for k, bk in enumerate(b))
+    den = 1.0 + sum(ak * z ** (k + 1) for k, ak in enumerate(a))
+    return 2.0 * (num / den).real
+
+
+def test_committed_impulse_mse_fits():
+    # the paper's own objective (reading 20): mean (H(w) - w)^2 on a uniform grid, recomputed
+    # here from the coefficients; stable, zero DC, and it trades the low frequencies away
+    with open(os.path.join(ROOT, "paper_2007_06289_gb300", "iir_coeffs_mse.json")) as fh:
+        table = json.load(fh)
+    assert sorted(e["N"] for e in table["entries"]) == [256, 512, 1024, 2048]
+    for e in table["entries"]:
+        b, a, M = np.array(e["b"]), np.array(e["a"]), e["M"]
+        assert np.abs(np.roots(np.concatenate([[1.0], a]))).max() < 1.0
+        assert abs(b.sum()) <= 1e-12
+        w = (np.arange(2 * M) + 0.5) / (4.0 * M)
+        loss = float(np.mean((_response(b, a, w) - w) ** 2))
+        assert abs(loss - e["loss"]) <= 1e-9 * max(1.0, loss)
+        lo = w < 1.0 / M                                   # the lowest frequencies
+        assert np.abs(_response(b, a, w[lo]) / w[lo] - 1).max() > 0.5
+
+
+def test_committed_direct_fits_are_stable_and_zero_dc():
+    with open(os.path.join(ROOT, "paper_2007_06289_gb300", "iir_direct_coeffs.json")) as fh:
+        table = json.load(fh)
+    have = {(e["N"], e["order"]) for e in table["entries"]}
+    assert have == {(N, o) for N in (256, 512, 1024, 2048) for o in (3, 6)}
+    for e in table["entries"]:
+        b, a = np.array(e["b"]), np.array(e["a"])
+        assert len(b) == e["order"] and len(a) == e["order"]
+        assert np.abs(np.roots(np.concatenate([[1.0], a]))).max() < 0.99995
+        assert abs(b.sum()) <= 1e-9 * np.abs(b).sum()
+        assert e["loss"] <= e["loss_start_projected"] * (1 + 1e-9)

@@ -344,6 +344,39 @@ def test_direct_fbp_matches_oracle(fbp, torch):
             assert np.abs(got[ys, xs] - want).max() <= TOL_DIRECT * (got.max() - got.min())
 
 
+def test_direct_fbp_partial_tile_sizes(fbp, torch):
+    # sizes below and across the comparator's 32 x 32 pixel tile and 32-angle blocks
+    for N, K, M in ((2, 3, 3), (16, 24, 23), (32, 37, 67), (64, 31, 129)):
+        s = phantoms.ellipse_sinogram(phantoms.random_ellipses(N + 1), N, K, M).astype(np.float32)
+        plan = fbp.fbp_plan(N, K, M, 1)
+        img = torch.empty(plan.img_shape, device="cuda")
+        fbp.fbp_direct_reconstruct(plan, dev(torch, s[None]), img)
+        torch.cuda.synchronize()
+        want = oracle.direct_fbp(s.astype(np.float64), N)
+        assert np.abs(host(img)[0] - want).max() <= TOL_DIRECT * max(want.max() - want.min(), 1e-6)
+
+
+def test_exact_fir_filter_matches_oracle(fbp, torch):
+    # fbp_filter_fir: the exact ramp filter of Eq. 8 over whole rows (the comparator's filter).
+    # A float32 sum of up to M terms with heavy cancellation: each output is bounded by
+    # 2^-14 of the sum of its terms' magnitudes, sum_k |h(k)| |p(n-k)| (the recursive-sum
+    # bound M 2^-24 of that sum is 2^-13.5 at M = 1449); a wrong tap or bin is off by a
+    # whole term.
+    from scipy.signal import fftconvolve
+    for N in (64, 1024):
+        K, M = phantoms.geometry_for(N)
+        s = phantoms.ellipse_sinogram(phantoms.random_ellipses(N + 7), N, K, M, 1e5, 3).astype(np.float32)
+        plan = fbp.fbp_plan(N, K, M, 1)
+        out = torch.empty(plan.sino_shape, device="cuda")
+        fbp.fbp_filter_fir(plan, dev(torch, s[None]), out)
+        s64 = s.astype(np.float64)
+        want = oracle.fir_ramp(s64)
+        habs = np.abs(oracle.ramp_h(np.arange(-(M - 1), M)))
+        mag = fftconvolve(np.abs(s64), habs[None, :], mode="same", axes=1)
+        err = np.abs(host(out)[0] - want)
+        assert np.all(err <= 2.0 ** -14 * mag), float((err / mag).max())
+
+
 # ------------------------------------------------------------------ ABI behaviour on a GPU
 def test_misaligned_and_workspace(fbp, torch):
     N = 64
