@@ -2,35 +2,45 @@
 // (1 -> 32 -> 32 -> 32 -> 32 -> 32 -> 1 channels, ReLU between, zero padding) whose output
 // is added to the input image, y = x + net(x); forward and gradients for training.
 //
-// Hidden activation layout ("records"): bf16, per image four planes of 8 channels each
-// (plane p holds channels 8p .. 8p+7, one pixel's 8 channels = one 16-byte record).  A plane
-// is a zero-padded raster of (N+2) x (N+2) records -- pixel (y, x), y, x in [-1, N], at record
-// kRecGuard + (y+1)(N+2) + (x+1) -- with kRecGuard zero records before it and a zero tail after.
-// Every record that is not an image pixel is zero, so a 3x3 tap never needs a bounds test.
+// Hidden activation layout ("records"): bf16, one 64-byte record per pixel holding its 32
+// channels, the record's four 16-byte chunks (channels 8c .. 8c+7) stored XOR-permuted:
+// chunk c of record r at chunk position c ^ ((r >> 1) & 3) -- the 64-byte swizzle of the
+// tensor cores' shared-memory operands, applied in global memory already.  An image is a
+// zero-padded raster of (N+2) x (N+2) records -- pixel (y, x), y, x in [-1, N], at record
+// kRecGuard + (y+1)(N+2) + (x+1) -- with kRecGuard zero records before it and a zero tail
+// after.  Every record that is not an image pixel is zero, so a 3x3 tap never needs a
+// bounds test.
 //
 // The four 32 -> 32 layers run on the tcgen05 tensor cores as implicit GEMMs over the padded
-// raster.  An output tile is 128 consecutive records of one image (about 128 / (N+2) rows,
-// straddling row ends: pad records are computed and written back as zero).  For tap (dy,dx)
-// the A operand is the 128 records starting dx records after the start of "run" dy, the
-// 130 records from (tile start) + (dy-1)(N+2) - 1: three runs per plane cover all nine taps.
-// A run is one contiguous 2080-byte bulk copy, and in shared memory a run of one plane is a
-// stack of 8-row x 16-byte core matrices, i.e. the canonical K-major no-swizzle layout with
-// the 8-row group stride (SBO) 128 bytes and the K-chunk stride (LBO) the 2080 bytes between
-// the planes' copies of that run.  So every tap and every 16-channel K step is one
-// tcgen05.mma (M = 128 records, N = 32 output channels, K = 16) whose A descriptor is just
-// an address offset: 18 MMAs per tile, accumulating in TMEM (fp32, 32 columns per tile,
-// two tiles double-buffered).  The layer's weights (32 x 288 bf16, 18 KB) are one bulk copy
-// per CTA in the same layout (K chunk = tap x 4 + plane, 512 bytes apart).
+// raster, with the pixels as the MMA's N dimension: an MMA costs about the same up to
+// N = 128 whatever its width, so each one should carry as many pixels as it can.  An output
+// tile is 254 consecutive records of one image (straddling row ends: pad records are
+// computed and written back as zero).  "Run" dy is the 256 records from (tile start) +
+// (dy-1)(N+2) - 1, one contiguous 16-KB bulk copy placed in shared memory so that its row
+// index is congruent to its record index mod 8: the records then sit exactly in the
+// canonical K-major 64-byte-swizzled layout (8-row atoms of 512 bytes, row = one pixel's 32
+// channels) and serve as the B operand (N = 256 rows).  The A operand (M = 128 rows) stacks
+// the layer's weights for the three horizontal taps dx of one dy: row 32q + 8dx + o' holds
+// output channel 8q + o' at tap (dy, dx) (rows 32q + 24 .. 32q + 31 are zero).  So one MMA
+// per dy and 16-channel step, 6 per tile, accumulates D[(q, dx, o')][j] = the tile's
+// contribution of tap column dx at run row j, in TMEM (fp32, 256 columns).  The output
+// pixel i of the tile is D[dx = 0][i] + D[dx = 1][i + 1] + D[dx = 2][i + 2]: the epilogue
+// reads TMEM with the 16x256b shape, which gives one thread the rows of taps 0 and 1 of
+// one channel at the same two columns (and, from the upper 16 lanes, tap 2), so the sum
+// needs the neighbouring column pair only: two warp shuffles per 8 columns.  A stmatrix
+// transpose turns each warp's [channel][pixel] block into the 16-byte chunks of the pixel
+// records it stores.  The weights (128 x 96 bf16 = 24 KB) are one bulk copy per CTA in the
+// K-major layout without swizzle (K chunk = dy x 4 + input channel / 8, 2 KB apart).
 //
 // CTA roles (persistent, one CTA per SM): warp 0 lane 0 issues the bulk copies of each
-// tile's 12 runs into a 6-stage ring (mbarrier with transaction bytes); warp 1 owns the TMEM
-// allocation and its lane 0 issues the MMAs and commits them to the stage's "empty" and the
-// accumulator's "full" barriers; two epilogue warpgroups (warps 2-5 and 6-9, each warp one
-// TMEM lane quarter) take alternate tiles from four accumulators, read them with
-// tcgen05.ld, add bias, apply ReLU or the backward mask, and store the tile's four planes as
-// 16-byte records (zero for pad records).  Every wait is bounded
-// (about a second); on expiry the CTA sets the corrector's status word, the other roles
-// leave their loops, outstanding copies and MMAs are waited for, and TMEM is freed.
+// tile's 3 runs into a 3-stage ring (mbarrier with transaction bytes); warp 1 owns the TMEM
+// allocation (two 256-column accumulators) and its lane 0 issues the MMAs and commits them
+// to the stage's "empty" and the accumulator's "full" barriers; four epilogue warpgroups
+// (warps 2-17, each warp one TMEM lane quarter) share every tile, each taking 64 of its 256
+// columns, read them with tcgen05.ld, add bias, apply ReLU or the backward mask, and store
+// the tile's records (zero for pad records).  Every wait is bounded (about a second); on
+// expiry the CTA sets the corrector's status word, the other roles leave their loops,
+// outstanding copies and MMAs are waited for, and TMEM is freed.
 //
 // The 1 -> 32 and 32 -> 1 layers, the last layer's gradient and the weight gradients run on
 // the CUDA cores in fp32.  The data gradient of a 32 -> 32 layer is the same tensor-core
@@ -50,20 +60,28 @@ namespace {
 
 constexpr int kC = 32;            // hidden channels
 constexpr int kTaps = 9;
-constexpr int kPlanes = kC / 8;   // 16-byte records per pixel
-constexpr int kRecGuard = 8;         // zero records before the padded raster
-constexpr int kTileM = 128;       // records per tensor-core tile (MMA M)
-constexpr int kRun = kTileM + 2;  // records per run (tile plus the two horizontal taps)
-constexpr int kRunBytes = kRun * 16;
-constexpr int kStageBytes = 3 * kPlanes * kRunBytes;       // 24960
-constexpr int kStages = 6;
-constexpr int kWChunks = kTaps * kPlanes;                  // 36 K chunks of 8
-constexpr int kWBytes = kWChunks * kC * 16;                // 18432
-constexpr int kAcc = 4;           // TMEM accumulators (32 columns each)
-constexpr int kEpiGroups = 2;     // epilogue warpgroups; group g takes the tiles i = g mod 2
+constexpr int kPlanes = kC / 8;   // 16-byte chunks per pixel record
+constexpr int kRecGuard = 8;      // zero records before the padded raster
+constexpr int kTileOut = 254;     // output records per tensor-core tile
+constexpr int kNpix = 256;        // run rows per MMA (its N)
+constexpr int kRecBytes = 64;     // one pixel's 32 bf16 channels
+constexpr int kRunCopy = kNpix * kRecBytes;                // 16384 bytes per run copy
+constexpr int kRunBytes = 264 * kRecBytes;                 // run buffer: 7 rows of phase + 256, in atoms
+constexpr int kStageBytes = 3 * kRunBytes;                 // 50688
+constexpr int kStages = 3;
+constexpr int kWRows = 128;                                // A rows: (lane quarter, dx, channel)
+constexpr int kWChunks = 3 * kPlanes;                      // 12 K chunks of 8: (dy, input channel / 8)
+constexpr int kWBytes = kWChunks * kWRows * 16;            // 24576
+constexpr int kAcc = 2;           // TMEM accumulators (256 columns each)
+constexpr int kTmemCols = 512;
+constexpr int kEpiGroups = 4;     // epilogue warpgroups, all sharing every tile
+constexpr int kChunksPerEpi = kNpix / 32 / kEpiGroups;     // 32-column chunks per warp and tile
+static_assert(kChunksPerEpi == 2, "each epilogue warp reads two chunks with one batch of loads");
 constexpr int kConvThreads = 64 + 128 * kEpiGroups;
 constexpr int kBarriers = 2 * kStages + 2 * kAcc + 2;
-constexpr size_t kConvSmem = (size_t)kWBytes + (size_t)kStages * kStageBytes + kBarriers * 8 + 16;
+constexpr int kScratchBytes = 4 * kEpiGroups * 512;        // per epilogue warp: 32 pixels x 8 channels bf16
+constexpr size_t kConvSmem = 1024 + (size_t)kWBytes + (size_t)kStages * kStageBytes + kScratchBytes +
+                             kBarriers * 8 + 16;
 constexpr int kTileY = 8, kTileX = 16;           // pixels per tile of the weight-gradient kernel
 constexpr int kHaloY = kTileY + 2, kHaloX = kTileX + 2;
 
@@ -82,8 +100,8 @@ __host__ __device__ inline ActGeom act_geom(int N)
     ActGeom g;
     g.N = N;
     g.W = N + 2;
-    g.T = (int)(((long long)N * g.W + kTileM - 1) / kTileM);
-    const long long need = kRecGuard + 2LL * g.W + (long long)kTileM * g.T + 8;
+    g.T = (int)(((long long)N * g.W + kTileOut - 1) / kTileOut);
+    const long long need = kRecGuard + 2LL * g.W + (long long)kTileOut * g.T + 8;
     g.plane = (need + 7) & ~7LL;
     return g;
 }
@@ -92,6 +110,9 @@ __host__ __device__ inline long long rec_index(const ActGeom& g, int y, int x)
 {
     return kRecGuard + (long long)(y + 1) * g.W + (x + 1);
 }
+
+// position of chunk c (channels 8c .. 8c+7) within record r
+__host__ __device__ inline int chunk_pos(long long r, int c) { return c ^ (int)((r >> 1) & 3); }
 
 // ---------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -188,10 +209,18 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// The same for the 64-byte-swizzled K-major layout: 8-row atoms of 512 bytes (SBO), the
+// swizzle taken from the address bits (a start at any 64-byte row, plus 32 bytes per K step).
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+           (1ull << 46) | (4ull << 61);
+}
+
 // Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both K-major,
-// N = 32, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kC >> 3) << 17) |
-                            ((uint32_t)(kTileM >> 4) << 24);
+// N = 256 (pixels), M = 128 (weight rows).
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kNpix >> 3) << 17) |
+                            ((uint32_t)(kWRows >> 4) << 24);
 
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t acc)
 {
@@ -206,9 +235,11 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar)
                  ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
+// 16x256b shapes: thread t receives TMEM lane (base + t/4) at columns 2(t%4), 2(t%4)+1 and
+// lane (base + 8 + t/4) at the same columns; each further repetition is 8 columns on.
+__device__ __forceinline__ void tmem_ld16_x8(uint32_t taddr, uint32_t* v)
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x8.b32 "
                  "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
                  "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
@@ -218,7 +249,27 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32])
                    "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
                    "=r"(v[30]), "=r"(v[31])
                  : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld16_x1(uint32_t taddr, uint32_t* v)
+{
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld()
+{
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Four 8 x 8 bf16 matrices, fragment of thread t = (row t / 4, columns 2(t % 4), +1), stored
+// transposed: row j of matrix i (the fragment's column j) to the 16 bytes at the address
+// that thread 8i + j supplies.
+__device__ __forceinline__ void stmatrix_x4_trans(uint32_t addr, uint32_t r0, uint32_t r1, uint32_t r2,
+                                                  uint32_t r3)
+{
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1,%2,%3,%4};"
+                 ::"r"(addr), "r"(r0), "r"(r1), "r"(r2), "r"(r3) : "memory");
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
@@ -239,22 +290,29 @@ __device__ __forceinline__ void unpack_record(const uint4 r, float* v)
 }
 
 // ---------------------------------------------------------------- weight preparation
-// fp32 [co][ci][3][3] of a 32 -> 32 layer -> the shared-memory image of the GEMM's B operand:
-// K chunk c = tap * 4 + (input channel / 8), then output channel, then input channel % 8.
-// Forward: output channel co, input ci, tap.  Data gradient (transposed convolution): output
-// channel ci, input co, tap 8 - tap.
+// fp32 [co][ci][3][3] of a 32 -> 32 layer -> the shared-memory image of the GEMM's A operand:
+// K chunk (dy * 4 + input channel / 8), then row 32 (o / 8) + 8 dx + o % 8, then input
+// channel % 8 (rows 32 q + 24 .. 32 q + 31 zero).  Forward: output o = co, input ci, tap
+// (dy, dx).  Data gradient (transposed convolution): output o = ci, input co, tap
+// (2 - dy, 2 - dx).  One thread per element of the image.
 __global__ void cnn_prep_weights_kernel(const float* __restrict__ w, bf16* __restrict__ fwd,
                                         bf16* __restrict__ bwd)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;      // co, ci, tap
-    if (e >= kC * kC * kTaps) return;
-    const int tap = e % kTaps;
-    const int ci = (e / kTaps) % kC;
-    const int co = e / (kTaps * kC);
-    const bf16 v = __float2bfloat16_rn(w[e]);
-    fwd[((tap * kPlanes + ci / 8) * kC + co) * 8 + ci % 8] = v;
-    const int mt = kTaps - 1 - tap;
-    bwd[((mt * kPlanes + co / 8) * kC + ci) * 8 + co % 8] = v;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;      // (chunk, row, lane of 8)
+    if (e >= kWChunks * kWRows * 8) return;
+    const int c8 = e & 7;
+    const int row = (e >> 3) % kWRows;
+    const int chunk = e / (8 * kWRows);
+    const int dy = chunk / kPlanes, cin = (chunk % kPlanes) * 8 + c8;
+    const int q = row / 32, dx = (row % 32) / 8, ol = row % 8;
+    const int o = 8 * q + ol;
+    float vf = 0.0f, vb = 0.0f;
+    if (dx < 3) {
+        vf = w[((o * kC + cin) * 3 + dy) * 3 + dx];              // W[o][cin][dy][dx]
+        vb = w[((cin * kC + o) * 3 + (2 - dy)) * 3 + (2 - dx)];  // W[cin][o][2-dy][2-dx]
+    }
+    fwd[e] = __float2bfloat16_rn(vf);
+    bwd[e] = __float2bfloat16_rn(vb);
 }
 
 // ---------------------------------------------------------------- 32 -> 32 on tcgen05
@@ -271,10 +329,13 @@ template <bool BIAS, bool RELU, bool MASK>
 __global__ void __launch_bounds__(kConvThreads, 1)
 cnn_conv32_kernel(ConvArgs a)
 {
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // run buffers must start on 512-byte atoms: align the carve to 1 KB
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char* wsm = smem;
     unsigned char* stages = smem + kWBytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(stages + (size_t)kStages * kStageBytes);
+    unsigned char* scratch = stages + (size_t)kStages * kStageBytes;     // 512 bytes per epilogue warp
+    uint64_t* bars = reinterpret_cast<uint64_t*>(scratch + kScratchBytes);
     uint64_t* full = bars;                  // [kStages] runs landed
     uint64_t* empty = bars + kStages;       // [kStages] runs consumed by the MMAs
     uint64_t* tfull = bars + 2 * kStages;   // [kAcc] accumulator complete
@@ -295,7 +356,7 @@ cnn_conv32_kernel(ConvArgs a)
         }
         for (int b = 0; b < kAcc; ++b) {
             mbar_init(tfull + b, 1);
-            mbar_init(tempty + b, 4);
+            mbar_init(tempty + b, 4 * kEpiGroups);
         }
         mbar_init(wbar, 1);
         mbar_init(drain, 1);
@@ -304,7 +365,7 @@ cnn_conv32_kernel(ConvArgs a)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(smem_u32(tmem_slot)), "n"(kAcc * kC) : "memory");
+                     ::"r"(smem_u32(tmem_slot)), "n"(kTmemCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
@@ -314,7 +375,7 @@ cnn_conv32_kernel(ConvArgs a)
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---- producer: weights once, then the 12 runs of every tile
+            // ---- producer: weights once, then the 3 runs of every tile
             mbar_expect_tx(wbar, kWBytes);
             bulk_g2s(wsm, a.wimg, kWBytes, wbar);
             long long i = 0;
@@ -327,17 +388,15 @@ cnn_conv32_kernel(ConvArgs a)
                     while (tt >= G.T) { tt -= G.T; ++img; }
                 }
                 if (!wait_bar(empty + s, (k & 1u) ^ 1u, abort_flag)) break;
-                const long long m0 = kRecGuard + G.W + (long long)kTileM * tt;
-                mbar_expect_tx(full + s, kStageBytes);
+                const long long m0 = kRecGuard + G.W + (long long)kTileOut * tt;
+                mbar_expect_tx(full + s, 3 * kRunCopy);
                 unsigned char* dst = stages + (size_t)s * kStageBytes;
 #pragma unroll 1
-                for (int dy = 0; dy < 3; ++dy)
-#pragma unroll 1
-                    for (int p = 0; p < kPlanes; ++p) {
-                        const uint4* src = a.in + ((long long)img * kPlanes + p) * G.plane + m0 +
-                                           (long long)(dy - 1) * G.W - 1;
-                        bulk_g2s(dst + (dy * kPlanes + p) * kRunBytes, src, kRunBytes, full + s);
-                    }
+                for (int dy = 0; dy < 3; ++dy) {
+                    const long long r0 = m0 + (long long)(dy - 1) * G.W - 1;     // run start
+                    const uint4* src = a.in + ((long long)img * G.plane + r0) * kPlanes;
+                    bulk_g2s(dst + dy * kRunBytes + (int)(r0 & 7) * kRecBytes, src, kRunCopy, full + s);
+                }
             }
             // copies still in flight land before the CTA exits
             for (long long j = i - kStages; j < i; ++j)
@@ -346,31 +405,37 @@ cnn_conv32_kernel(ConvArgs a)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---- MMA issuer
+            // ---- MMA issuer: per tile 6 MMAs (3 runs x 2 channel halves), A the stacked
+            // weights of the run's three taps, B the run's 256 records
             if (wait_bar(wbar, 0, abort_flag)) {
                 tc_fence_after();
                 const uint32_t wbase = smem_u32(wsm);
                 const uint32_t sbase = smem_u32(stages);
                 long long i = 0;
+                int tt = (int)(blockIdx.x % G.T);
                 for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i) {
                     const int s = (int)(i % kStages);
-                    const uint32_t k = (uint32_t)(i / kStages);
                     const int b = (int)(i % kAcc);
-                    const uint32_t j = (uint32_t)(i / kAcc);
-                    if (!wait_bar(full + s, k & 1u, abort_flag)) break;
-                    if (!wait_bar(tempty + b, (j & 1u) ^ 1u, abort_flag)) break;
+                    if (i > 0) {                               // next tile of this CTA
+                        tt += gridDim.x;
+                        while (tt >= G.T) tt -= G.T;
+                    }
+                    const long long m0 = kRecGuard + G.W + (long long)kTileOut * tt;
+                    if (!wait_bar(full + s, (uint32_t)(i / kStages) & 1u, abort_flag)) break;
+                    if (!wait_bar(tempty + b, ((uint32_t)(i / kAcc) & 1u) ^ 1u, abort_flag)) break;
                     tc_fence_after();
-                    const uint32_t d = tmem + (uint32_t)(b * kC);
+                    const uint32_t d = tmem + (uint32_t)(b * kNpix);
                     const uint32_t abase = sbase + (uint32_t)(s * kStageBytes);
 #pragma unroll
-                    for (int tap = 0; tap < kTaps; ++tap) {
-                        const int dy = tap / 3, dx = tap % 3;
+                    for (int dy = 0; dy < 3; ++dy) {
+                        const uint32_t ph = (uint32_t)((m0 - 1 + (long long)(dy - 1) * G.W) & 7);
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk) {
-                            const uint32_t aa = abase + (uint32_t)((dy * kPlanes + 2 * kk) * kRunBytes + dx * 16);
-                            const uint32_t ba = wbase + (uint32_t)((tap * kPlanes + 2 * kk) * kC * 16);
-                            umma(d, smem_desc(aa, kRunBytes, 128), smem_desc(ba, kC * 16, 128),
-                                 (tap | kk) != 0 ? 1u : 0u);
+                            const uint64_t ad = smem_desc(wbase + (uint32_t)((dy * kPlanes + 2 * kk) * kWRows * 16),
+                                                          kWRows * 16, 128);
+                            const uint64_t bd = smem_desc_sw64(abase + (uint32_t)(dy * kRunBytes) +
+                                                               ph * kRecBytes + 32u * kk);
+                            umma(d, ad, bd, (dy | kk) != 0 ? 1u : 0u);
                         }
                     }
                     umma_commit(empty + s);
@@ -381,74 +446,126 @@ cnn_conv32_kernel(ConvArgs a)
             drain_bar(drain, 0);                // ... once this phase does
         }
     } else {
-        // ---- epilogue: warpgroup eg (warps 2+4eg .. 5+4eg) takes tiles i = eg mod 2; each
-        // warp reads TMEM lane quarter warp % 4
+        // ---- epilogue: warpgroup eg (warps 2+4eg .. 5+4eg) takes every tile, 32-column
+        // chunks [c0, c0 + 2) of it; each warp reads TMEM lane quarter warp % 4
         const int q = warp & 3;
-        const int row = 32 * q + lane;
         const int eg = (warp - 2) >> 2;
         const int etid = threadIdx.x - 64;               // 0 .. 128 kEpiGroups - 1
         // zero the records no tile writes: the guard and top pad row, and the tail
         const long long head = kRecGuard + G.W;
-        const long long tail0 = kRecGuard + G.W + (long long)kTileM * G.T;
+        const long long tail0 = kRecGuard + G.W + (long long)kTileOut * G.T;
         const long long tail = G.plane - tail0;
-        const long long nz = (long long)a.images * kPlanes * (head + tail);
+        const long long nz = (long long)a.images * (head + tail) * kPlanes;      // 16-byte chunks
         for (long long z = (long long)blockIdx.x * (128 * kEpiGroups) + etid; z < nz;
              z += (long long)gridDim.x * (128 * kEpiGroups)) {
-            const long long pl = z / (head + tail);
-            const long long r = z - pl * (head + tail);
-            a.out[pl * G.plane + (r < head ? r : tail0 + (r - head))] = make_uint4(0u, 0u, 0u, 0u);
+            const long long rec = z / kPlanes;
+            const int part = (int)(z - rec * kPlanes);
+            const long long im = rec / (head + tail);
+            const long long r = rec - im * (head + tail);
+            a.out[(im * G.plane + (r < head ? r : tail0 + (r - head))) * kPlanes + part] =
+                make_uint4(0u, 0u, 0u, 0u);
         }
-        float bias[kC];
-#pragma unroll
-        for (int c = 0; c < kC; ++c) bias[c] = BIAS ? __ldg(a.bias + c) : 0.0f;
-        long long i = eg;
-        int img = (int)((blockIdx.x + (long long)eg * gridDim.x) / G.T);
-        int tt = (int)((blockIdx.x + (long long)eg * gridDim.x) % G.T);
-        const int step = kEpiGroups * gridDim.x;
-        for (long long t = blockIdx.x + (long long)eg * gridDim.x; t < total;
-             t += step, i += kEpiGroups) {
-            if (i != eg) {                               // next tile of this warpgroup
-                tt += step;
+        // TMEM lane 32q + 8dx + g holds output channel 8q + g at tap dx (dx = 3: zero rows).
+        // With the 16x256b loads lane t of the warp holds, for g = t / 4 and every group of 8
+        // columns, columns 2m and 2m + 1 (m = t % 4) of taps 0 and 1 (load P, lanes 32q ..
+        // 32q + 15) and of tap 2 (load Q, lanes 32q + 16 ..).  Output pixel k needs tap dx at
+        // column k + dx: for the pair (2m, 2m + 1) the columns 2m + 2, 2m + 3 come from the
+        // neighbour m + 1, or for m = 3 from lane m = 0's next group.
+        const int g = lane >> 2, m = lane & 3;
+        const int nb = (lane & ~3) | ((lane + 1) & 3);
+        const int c0 = eg * kChunksPerEpi;               // this group's first 32-column chunk
+        const float bias = BIAS ? __ldg(a.bias + 8 * q + g) : 0.0f;
+        unsigned char* scr = scratch + (size_t)(warp - 2) * 512;    // [32 px][8 ch] bf16
+        long long i = 0;
+        int img = (int)(blockIdx.x / G.T), tt = (int)(blockIdx.x % G.T);
+        for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+            if (i > 0) {                                 // next tile of this CTA
+                tt += gridDim.x;
                 while (tt >= G.T) { tt -= G.T; ++img; }
             }
             const int b = (int)(i % kAcc);
             const uint32_t j = (uint32_t)(i / kAcc);
             if (!wait_bar(tfull + b, j & 1u, abort_flag)) break;
             tc_fence_after();
-            uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kC), v);
+            const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kNpix);
+            // groups 4c0 .. 4c0 + 7 and the first group after them (none after the last chunk)
+            constexpr int R = 8;
+            uint32_t P[4 * R + 4], Q[4 * R + 4];
+            tmem_ld16_x8(tb + (uint32_t)(32 * c0), P);
+            tmem_ld16_x8(tb + (16u << 16) + (uint32_t)(32 * c0), Q);
+            if (c0 + kChunksPerEpi < kNpix / 32) {
+                tmem_ld16_x1(tb + (uint32_t)(32 * (c0 + kChunksPerEpi)), P + 4 * R);
+                tmem_ld16_x1(tb + (16u << 16) + (uint32_t)(32 * (c0 + kChunksPerEpi)), Q + 4 * R);
+            } else {
+#pragma unroll
+                for (int u = 4 * R; u < 4 * R + 4; ++u) P[u] = Q[u] = 0u;
+            }
+            tmem_wait_ld();
+            // the accumulator is in registers: hand it back to the MMAs
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty + b);
-            // pixel of this record: 32-bit arithmetic (a plane has < 2^31 records)
-            const unsigned rel = (unsigned)(G.W + kTileM * tt + row);
-            const unsigned yy = rel / (unsigned)G.W;
-            const int y = (int)yy - 1;
-            const int x = (int)(rel - yy * (unsigned)G.W) - 1;
-            const long long m = kRecGuard + (long long)rel;
-            const bool inside = (unsigned)y < (unsigned)a.N && (unsigned)x < (unsigned)a.N;
-            float mk[kC];
-            if (MASK && inside) {
+            // in group r this lane holds tap 0 at columns 2m, 2m + 1 (P[4r], P[4r + 1]), tap 1
+            // (P[4r + 2], P[4r + 3]) and tap 2 (Q[4r], Q[4r + 1]).  Outputs 2m and 2m + 1:
+            //   out(2m)     = (t0(2m) + t1(2m + 1)) + t2(2m + 2)
+            //   out(2m + 1) = t0(2m + 1) + (t1(2m + 2) + t2(2m + 3))
+            // the terms of columns 2m + 2, 2m + 3 come from the neighbour m + 1, which sends
+            // t2 at its column 2(m+1) and its own sum t1(2(m+1)) + t2(2(m+1) + 1).
+            float pre[R + 1];
 #pragma unroll
-                for (int p = 0; p < kPlanes; ++p)
-                    unpack_record(a.mask[((long long)img * kPlanes + p) * G.plane + m], mk + 8 * p);
-            }
+            for (int r = 0; r <= R; ++r)
+                pre[r] = __uint_as_float(P[4 * r + 2]) + __uint_as_float(Q[4 * r + 1]);
+            // padded-raster position (yy, xx) of this lane's pixel of the first chunk: record
+            // kRecGuard + yy W + xx
+            const unsigned rel = (unsigned)(G.W + kTileOut * tt + 32 * c0 + lane);
+            unsigned yy = rel / (unsigned)G.W;
+            unsigned xx = rel - yy * (unsigned)G.W;
 #pragma unroll
-            for (int p = 0; p < kPlanes; ++p) {
-                uint32_t w4[4];
+            for (int h = 0; h < kChunksPerEpi; ++h) {
+                uint32_t packed[4];
 #pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const int c = 8 * p + 2 * h;
-                    float v0 = __uint_as_float(v[c]), v1 = __uint_as_float(v[c + 1]);
-                    if (BIAS) { v0 += bias[c]; v1 += bias[c + 1]; }
-                    if (RELU) { v0 = fmaxf(v0, 0.0f); v1 = fmaxf(v1, 0.0f); }
-                    if (MASK) {
-                        v0 = mk[c] > 0.0f ? v0 : 0.0f;
-                        v1 = mk[c + 1] > 0.0f ? v1 : 0.0f;
-                    }
-                    w4[h] = inside ? pack_bf16(v0, v1) : 0u;
+                for (int r4 = 0; r4 < 4; ++r4) {
+                    const int r = 4 * h + r4;
+                    const uint32_t sa = m == 0 ? Q[4 * r + 4] : Q[4 * r];
+                    const float sb = m == 0 ? pre[r + 1] : pre[r];
+                    const float xa = __uint_as_float(__shfl_sync(0xffffffffu, sa, nb));
+                    const float xb = __shfl_sync(0xffffffffu, sb, nb);
+                    float o0 = (__uint_as_float(P[4 * r]) + __uint_as_float(P[4 * r + 3])) + xa;
+                    float o1 = __uint_as_float(P[4 * r + 1]) + xb;
+                    if (BIAS) { o0 += bias; o1 += bias; }
+                    __nv_bfloat162 pk = __floats2bfloat162_rn(o0, o1);
+                    // ReLU after rounding: rounding is monotone and keeps 0, so this equals
+                    // rounding the rectified value
+                    if (RELU) pk = __hmax2(pk, __floats2bfloat162_rn(0.0f, 0.0f));
+                    packed[r4] = *reinterpret_cast<const uint32_t*>(&pk);
                 }
-                a.out[((long long)img * kPlanes + p) * G.plane + m] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                // group r is an 8 x 8 matrix [channel g][pixel 8r + j]: stored transposed, the
+                // scratch holds [pixel][channel], i.e. the 16-byte chunk q of 32 pixel records
+                stmatrix_x4_trans(smem_u32(scr) + 16u * lane, packed[0], packed[1], packed[2], packed[3]);
+                __syncwarp();
+                const uint4 wv = reinterpret_cast<const uint4*>(scr)[lane];      // pixel 32(c0+h) + lane
+                __syncwarp();
+                uint32_t w4[4] = {wv.x, wv.y, wv.z, wv.w};
+                const int px = 32 * (c0 + h) + lane;                 // output of the tile
+                const int y = (int)yy - 1, x = (int)xx - 1;
+                const long long mrec = kRecGuard + (long long)yy * G.W + xx;
+                xx += 32;
+                while (xx >= (unsigned)G.W) { xx -= (unsigned)G.W; ++yy; }
+                if (px < kTileOut) {
+                    const bool inside = (unsigned)y < (unsigned)a.N && (unsigned)x < (unsigned)a.N;
+                    const long long rec = ((long long)img * G.plane + mrec) * kPlanes + chunk_pos(mrec, q);
+                    if (MASK && inside) {
+                        const uint4 mr = a.mask[rec];
+                        const uint32_t mw[4] = {mr.x, mr.y, mr.z, mr.w};
+#pragma unroll
+                        for (int hh = 0; hh < 4; ++hh) {
+                            const float2 mf = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&mw[hh]));
+                            const uint32_t keep = (mf.x > 0.0f ? 0x0000ffffu : 0u) | (mf.y > 0.0f ? 0xffff0000u : 0u);
+                            w4[hh] &= keep;
+                        }
+                    }
+                    a.out[rec] = inside ? make_uint4(w4[0], w4[1], w4[2], w4[3]) : make_uint4(0u, 0u, 0u, 0u);
+                }
             }
         }
     }
@@ -456,7 +573,7 @@ cnn_conv32_kernel(ConvArgs a)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kAcc * kC) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTmemCols) : "memory");
     }
 }
 
@@ -514,7 +631,7 @@ cnn_first_kernel(const float* __restrict__ x, const float* __restrict__ w,
             }
         }
     }
-    uint4* dst = h + (long long)img * kPlanes * G.plane;
+    uint4* dst = h + (long long)img * G.plane * kPlanes;
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         const long long r = r0 + u * kFirstStride;
@@ -527,21 +644,20 @@ cnn_first_kernel(const float* __restrict__ x, const float* __restrict__ w,
                 const int o = 8 * p + 2 * hh;
                 w4[hh] = inside[u] ? pack_bf16(fmaxf(acc[u][o], 0.0f), fmaxf(acc[u][o + 1], 0.0f)) : 0u;
             }
-            dst[p * G.plane + r] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            dst[r * kPlanes + chunk_pos(r, p)] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
         }
     }
 }
 
-// the 32 channels of record r of one image's planes
-__device__ __forceinline__ void load_pixel32(float (&v)[kC], const uint4* planes, long long plane,
-                                             long long r)
+// the 32 channels of record r of one image's records
+__device__ __forceinline__ void load_pixel32(float (&v)[kC], const uint4* recs, long long r)
 {
 #pragma unroll
-    for (int p = 0; p < kPlanes; ++p) unpack_record(planes[p * plane + r], v + 8 * p);
+    for (int p = 0; p < kPlanes; ++p) unpack_record(recs[r * kPlanes + chunk_pos(r, p)], v + 8 * p);
 }
 
 // Last layer and the skip connection: y[p] = x[p] + b + sum_{tap, c} w[c][tap] h[p + off][c].
-// One 16 x 16 output tile per CTA: its 18 x 18 records (four planes) are staged in shared
+// One 16 x 16 output tile per CTA: its 18 x 18 records (four chunks each) are staged in shared
 // memory once; the weights sit there as [tap][c] and reach registers as 16-byte broadcasts;
 // each thread sums the 9 taps x 32 channels of two pixels, rows ly and ly + 8 (pad records
 // are zero: no bounds tests).
@@ -558,11 +674,12 @@ cnn_last_kernel(const float* __restrict__ x, const uint4* __restrict__ h, const 
     const ActGeom G = act_geom(N);
     const int tiles_x = N / kLT;
     const int y0 = (int)(blockIdx.x / tiles_x) * kLT, x0 = (int)(blockIdx.x % tiles_x) * kLT;
-    const uint4* hp = h + (long long)blockIdx.y * kPlanes * G.plane;
+    const uint4* hp = h + (long long)blockIdx.y * G.plane * kPlanes;
     for (int e = threadIdx.x; e < kPlanes * kLH * kLH; e += blockDim.x) {
-        const int p = e / (kLH * kLH), r = e - p * (kLH * kLH);
+        const int r = e / kPlanes, p = e - r * kPlanes;
         const int ty = r / kLH, tx = r - ty * kLH;
-        hs[p][r] = hp[p * G.plane + rec_index(G, y0 - 1 + ty, x0 - 1 + tx)];
+        const long long rec = rec_index(G, y0 - 1 + ty, x0 - 1 + tx);
+        hs[p][r] = hp[rec * kPlanes + chunk_pos(rec, p)];
     }
     __syncthreads();
     const int ly = threadIdx.x / kLT, lx = threadIdx.x % kLT;      // rows ly and ly + 8
@@ -610,11 +727,11 @@ cnn_last_backward_kernel(const float* __restrict__ gy, const uint4* __restrict__
         py = (int)yy - 1;
         px = (int)(u - yy * (unsigned)G.W) - 1;
     }
-    const long long ib = (long long)blockIdx.y * kPlanes * G.plane;
-    uint4* dst = g + ib + r;
+    const long long ib = (long long)blockIdx.y * G.plane * kPlanes;
+    uint4* dst = g + ib + r * kPlanes;
     if ((unsigned)py >= (unsigned)N || (unsigned)px >= (unsigned)N) {
 #pragma unroll
-        for (int p = 0; p < kPlanes; ++p) dst[p * G.plane] = make_uint4(0u, 0u, 0u, 0u);
+        for (int p = 0; p < kPlanes; ++p) dst[p] = make_uint4(0u, 0u, 0u, 0u);
         return;
     }
     const size_t img = (size_t)blockIdx.y * N * N;
@@ -625,7 +742,7 @@ cnn_last_backward_kernel(const float* __restrict__ gy, const uint4* __restrict__
         v[tap] = (yy >= 0 && yy < N && xx >= 0 && xx < N) ? gy[img + (size_t)yy * N + xx] : 0.0f;
     }
     float m[kC];
-    load_pixel32(m, h5 + ib, G.plane, r);
+    load_pixel32(m, h5 + ib, r);
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) {
         uint32_t w4[4];
@@ -640,7 +757,7 @@ cnn_last_backward_kernel(const float* __restrict__ gy, const uint4* __restrict__
             }
             w4[hh] = pack_bf16(m[c] > 0.0f ? s0 : 0.0f, m[c + 1] > 0.0f ? s1 : 0.0f);
         }
-        dst[p * G.plane] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        dst[chunk_pos(r, p)] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
     }
 }
 
@@ -649,9 +766,9 @@ cnn_last_backward_kernel(const float* __restrict__ gy, const uint4* __restrict__
 // of all images.  CO / CI are 32 or 1; a 1-channel operand is fp32 [N][N] (the image or the
 // output gradient), a 32-channel one records.  Persistent CTAs accumulate over 8 x 16-pixel
 // tiles in registers and add once into the global gradient.
-__device__ __forceinline__ float record_channel(const uint4* planes, long long plane, long long r, int c)
+__device__ __forceinline__ float record_channel(const uint4* recs, long long r, int c)
 {
-    const bf16* rec = reinterpret_cast<const bf16*>(planes + (c >> 3) * plane + r);
+    const bf16* rec = reinterpret_cast<const bf16*>(recs + r * kPlanes + chunk_pos(r, c >> 3));
     return __bfloat162float(rec[c & 7]);
 }
 
@@ -677,13 +794,13 @@ cnn_wgrad_kernel(const void* __restrict__ gz_, const void* __restrict__ hp_, flo
         const int rem = (int)(tile - (long long)im * tiles_x * tiles_y);
         const int y0 = (rem / tiles_x) * kTileY, x0 = (rem % tiles_x) * kTileX;
         const size_t img = (size_t)im * N * N;
-        const long long ib = (long long)im * kPlanes * G.plane;
+        const long long ib = (long long)im * G.plane * kPlanes;
         __syncthreads();                               // previous tile consumed
         for (int e = tid; e < kTileY * kTileX * CO; e += 256) {
             const int pix = e / CO, o = e - pix * CO;
             const int yy = y0 + pix / kTileX, xx = x0 + pix % kTileX;
             gzs[pix][o] = CO == 1 ? static_cast<const float*>(gz_)[img + (size_t)yy * N + xx]
-                                  : record_channel(static_cast<const uint4*>(gz_) + ib, G.plane,
+                                  : record_channel(static_cast<const uint4*>(gz_) + ib,
                                                    rec_index(G, yy, xx), o);
         }
         for (int e = tid; e < kHaloY * kHaloX * CI; e += 256) {
@@ -694,7 +811,7 @@ cnn_wgrad_kernel(const void* __restrict__ gz_, const void* __restrict__ hp_, flo
                 if (gy >= 0 && gy < N && gx >= 0 && gx < N)
                     v = static_cast<const float*>(hp_)[img + (size_t)gy * N + gx];
             } else {
-                v = record_channel(static_cast<const uint4*>(hp_) + ib, G.plane, rec_index(G, gy, gx), c);
+                v = record_channel(static_cast<const uint4*>(hp_) + ib, rec_index(G, gy, gx), c);
             }
             hps[pix][c] = v;
         }
@@ -822,7 +939,7 @@ cudaError_t forward(const float* params, const float* x, float* y, void* ws, int
 {
     Ws w = carve(ws, N, batch, save);
     for (int k = 0; k < 4; ++k)
-        cnn_prep_weights_kernel<<<(kC * kC * kTaps + 255) / 256, 256, 0, st>>>(
+        cnn_prep_weights_kernel<<<(kWChunks * kWRows * 8 + 255) / 256, 256, 0, st>>>(
             params + param_offset(k + 1), w.wf[k], w.wb[k]);
     const ActGeom G = act_geom(N);
     const dim3 fg((unsigned)((G.plane + 2 * kFirstStride - 1) / (2 * kFirstStride)), batch);
