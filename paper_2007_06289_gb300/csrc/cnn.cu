@@ -42,7 +42,9 @@
 // expiry the CTA sets the corrector's status word, the other roles leave their loops,
 // outstanding copies and MMAs are waited for, and TMEM is freed.
 //
-// The 1 -> 32 and 32 -> 1 layers, the last layer's gradient and the weight gradients run on
+// The 32 -> 1 layer runs in the same tensor-core kernel (its fp32 weights split exactly
+// into three bf16 parts, so that the products and their fp32 sums are those of the fp32
+// weights).  The 1 -> 32 layer, the last layer's gradient and the weight gradients run on
 // the CUDA cores in fp32.  The data gradient of a 32 -> 32 layer is the same tensor-core
 // kernel with the layer's weights transposed (input and output channels swapped, taps
 // mirrored) and the previous layer's ReLU applied as a mask.
@@ -251,6 +253,14 @@ __device__ __forceinline__ void tmem_ld16_x8(uint32_t taddr, uint32_t* v)
                  : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld16_x2(uint32_t taddr, uint32_t* v)
+{
+    asm volatile("tcgen05.ld.sync.aligned.16x256b.x2.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                   "=r"(v[6]), "=r"(v[7])
+                 : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_ld16_x1(uint32_t taddr, uint32_t* v)
 {
     asm volatile("tcgen05.ld.sync.aligned.16x256b.x1.b32 {%0,%1,%2,%3}, [%4];"
@@ -315,17 +325,51 @@ __global__ void cnn_prep_weights_kernel(const float* __restrict__ w, bf16* __res
     bwd[e] = __float2bfloat16_rn(vb);
 }
 
+// The 32 -> 1 layer in the same image: its fp32 weight w = W[0][cin][dy][dx] split exactly
+// into three bf16 parts, w = hi + mid + lo (hi = bf16(w), mid = bf16(w - hi), lo = bf16(w -
+// hi - mid): two bf16 parts leave at most 8 significant bits, which the third holds), as
+// "output channels" 0, 1, 2 (rows 32q + 8 dx + part) of every lane quarter q, so that all
+// epilogue warps can read them; the other rows zero.
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+__global__ void cnn_prep_last_kernel(const float* __restrict__ w, bf16* __restrict__ img)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;      // (chunk, row, lane of 8)
+    if (e >= kWChunks * kWRows * 8) return;
+    const int c8 = e & 7;
+    const int row = (e >> 3) % kWRows;
+    const int chunk = e / (8 * kWRows);
+    const int dy = chunk / kPlanes, cin = (chunk % kPlanes) * 8 + c8;
+    const int q = row / 32, dx = (row % 32) / 8, part = row % 8;
+    float v = 0.0f;
+    (void)q;
+    if (dx < 3 && part < 3) {
+        const float wv = w[(cin * 3 + dy) * 3 + dx];
+        const float hi = bf16_round(wv);
+        const float mid = bf16_round(wv - hi);
+        const float lo = bf16_round((wv - hi) - mid);
+        v = part == 0 ? hi : (part == 1 ? mid : lo);
+    }
+    img[e] = __float2bfloat16_rn(v);
+}
+
 // ---------------------------------------------------------------- 32 -> 32 on tcgen05
 struct ConvArgs {
     const uint4* in;        // records of `images` images
     const bf16* wimg;       // weight image (kWBytes)
-    const float* bias;      // [32] (BIAS)
+    const float* bias;      // [32] (BIAS), or the last layer's one bias (LAST)
     const uint4* mask;      // records (MASK): output channel c kept where mask's c > 0
-    uint4* out;             // records
+    uint4* out;             // records (not LAST)
+    const float* ximg;      // LAST: the corrector's input images [images][N][N]
+    float* yimg;            // LAST: its output y = x + conv(h) [images][N][N]
     int N, images;
 };
 
-template <bool BIAS, bool RELU, bool MASK>
+// LAST: the 32 -> 1 layer and the skip connection, y = x + b + conv(h), from the weight
+// image of cnn_prep_last_kernel: every lane quarter holds the same three rows, and epilogue
+// warp (q, eg) takes the 16 columns of groups 2(4 eg + q) and 2(4 eg + q) + 1, adds the
+// three weight parts and writes y.
+template <bool BIAS, bool RELU, bool MASK, bool LAST>
 __global__ void __launch_bounds__(kConvThreads, 1)
 cnn_conv32_kernel(ConvArgs a)
 {
@@ -455,7 +499,7 @@ cnn_conv32_kernel(ConvArgs a)
         const long long head = kRecGuard + G.W;
         const long long tail0 = kRecGuard + G.W + (long long)kTileOut * G.T;
         const long long tail = G.plane - tail0;
-        const long long nz = (long long)a.images * (head + tail) * kPlanes;      // 16-byte chunks
+        const long long nz = LAST ? 0 : (long long)a.images * (head + tail) * kPlanes;   // 16-byte chunks
         for (long long z = (long long)blockIdx.x * (128 * kEpiGroups) + etid; z < nz;
              z += (long long)gridDim.x * (128 * kEpiGroups)) {
             const long long rec = z / kPlanes;
@@ -474,7 +518,7 @@ cnn_conv32_kernel(ConvArgs a)
         const int g = lane >> 2, m = lane & 3;
         const int nb = (lane & ~3) | ((lane + 1) & 3);
         const int c0 = eg * kChunksPerEpi;               // this group's first 32-column chunk
-        const float bias = BIAS ? __ldg(a.bias + 8 * q + g) : 0.0f;
+        const float bias = BIAS ? __ldg(a.bias + 8 * q + g) : (LAST ? __ldg(a.bias) : 0.0f);
         unsigned char* scr = scratch + (size_t)(warp - 2) * 512;    // [32 px][8 ch] bf16
         long long i = 0;
         int img = (int)(blockIdx.x / G.T), tt = (int)(blockIdx.x % G.T);
@@ -485,6 +529,61 @@ cnn_conv32_kernel(ConvArgs a)
             }
             const int b = (int)(i % kAcc);
             const uint32_t j = (uint32_t)(i / kAcc);
+            if constexpr (LAST) {
+                // the skip input of this lane's pixel, loaded before the accumulator is waited
+                // for (its latency then overlaps the tile's matrix products)
+                const int r0 = 2 * (4 * eg + q);             // first of this warp's two groups
+                const int px = 8 * r0 + (lane & 15);         // output of the tile
+                const unsigned rl = (unsigned)(G.W + kTileOut * tt + px);
+                const unsigned ry = rl / (unsigned)G.W;
+                const int y = (int)ry - 1, x = (int)(rl - ry * (unsigned)G.W) - 1;
+                const bool ok = lane < 16 && px < kTileOut && (unsigned)y < (unsigned)a.N &&
+                                (unsigned)x < (unsigned)a.N;
+                const size_t pix = ok ? ((size_t)img * a.N + y) * a.N + x : 0;
+                const float xin = ok ? __ldg(a.ximg + pix) : 0.0f;
+                if (!wait_bar(tfull + b, j & 1u, abort_flag)) break;
+                tc_fence_after();
+                const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kNpix + 8 * r0);
+                uint32_t P[12], Q[12];
+                tmem_ld16_x2(tl, P);
+                tmem_ld16_x2(tl + (16u << 16), Q);
+                if (r0 + 2 < kNpix / 8) {
+                    tmem_ld16_x1(tl + 16u, P + 8);
+                    tmem_ld16_x1(tl + (16u << 16) + 16u, Q + 8);
+                } else {
+#pragma unroll
+                    for (int u = 8; u < 12; ++u) P[u] = Q[u] = 0u;
+                }
+                tmem_wait_ld();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty + b);
+                // taps summed as in the hidden layers; then channels g = 0, 1, 2 (the weight
+                // parts, lanes m, m + 4, m + 8) added: lanes 0..3 hold the conv at columns
+                // 8r + 2m, 8r + 2m + 1 of the warp's groups r = 0, 1
+                float* vs = reinterpret_cast<float*>(scr);     // [16]: the warp's pixels
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float pr0 = __uint_as_float(P[4 * r + 2]) + __uint_as_float(Q[4 * r + 1]);
+                    const float pr1 = __uint_as_float(P[4 * r + 6]) + __uint_as_float(Q[4 * r + 5]);
+                    const uint32_t sa = m == 0 ? Q[4 * r + 4] : Q[4 * r];
+                    const float sb = m == 0 ? pr1 : pr0;
+                    const float xa = __uint_as_float(__shfl_sync(0xffffffffu, sa, nb));
+                    const float xb = __shfl_sync(0xffffffffu, sb, nb);
+                    float o0 = (__uint_as_float(P[4 * r]) + __uint_as_float(P[4 * r + 3])) + xa;
+                    float o1 = __uint_as_float(P[4 * r + 1]) + xb;
+                    o0 = (o0 + __shfl_down_sync(0xffffffffu, o0, 4)) + __shfl_down_sync(0xffffffffu, o0, 8);
+                    o1 = (o1 + __shfl_down_sync(0xffffffffu, o1, 4)) + __shfl_down_sync(0xffffffffu, o1, 8);
+                    if (lane < 4) {
+                        vs[8 * r + 2 * m] = o0;
+                        vs[8 * r + 2 * m + 1] = o1;
+                    }
+                }
+                __syncwarp();
+                if (ok) a.yimg[pix] = xin + (vs[lane] + bias);
+                __syncwarp();
+                continue;
+            }
             if (!wait_bar(tfull + b, j & 1u, abort_flag)) break;
             tc_fence_after();
             const uint32_t tb = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kNpix);
@@ -581,7 +680,8 @@ cnn_conv32_kernel(ConvArgs a)
 // First layer: h[p][o] = relu(b[o] + sum_tap w[o][tap] x[p + off(tap)]), fp32 math, written
 // as records over the whole plane (zero outside the image).  The weights sit in shared
 // memory as [tap][o] and reach registers as 16-byte broadcasts, 32 per tap; each thread
-// computes the records r and r + kFirstStride.
+// computes the records r and r + kFirstStride, two output channels per packed fp32 FMA
+// (each channel's sum is the same chain of fmaf as one at a time).
 constexpr int kFirstStride = 128;           // records between a thread's two records
 __global__ void __launch_bounds__(128)
 cnn_first_kernel(const float* __restrict__ x, const float* __restrict__ w,
@@ -615,20 +715,20 @@ cnn_first_kernel(const float* __restrict__ x, const float* __restrict__ w,
             v[u][tap] = (inside[u] && yy >= 0 && yy < N && xx >= 0 && xx < N) ? xs[(size_t)yy * N + xx] : 0.0f;
         }
     }
-    float acc[2][kC];
+    float2 acc[2][kC / 2];                      // channels (2k, 2k + 1)
 #pragma unroll
-    for (int o = 0; o < kC; ++o) acc[0][o] = acc[1][o] = bs[o];
+    for (int k = 0; k < kC / 2; ++k) acc[0][k] = acc[1][k] = make_float2(bs[2 * k], bs[2 * k + 1]);
 #pragma unroll
     for (int tap = 0; tap < kTaps; ++tap) {
+        const float2 x0 = make_float2(v[0][tap], v[0][tap]), x1 = make_float2(v[1][tap], v[1][tap]);
 #pragma unroll
         for (int o4 = 0; o4 < kC; o4 += 4) {
             const float4 wv = *reinterpret_cast<const float4*>(&ws[tap][o4]);
-            const float wk[4] = {wv.x, wv.y, wv.z, wv.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                acc[0][o4 + k] = fmaf(wk[k], v[0][tap], acc[0][o4 + k]);
-                acc[1][o4 + k] = fmaf(wk[k], v[1][tap], acc[1][o4 + k]);
-            }
+            const float2 wa = make_float2(wv.x, wv.y), wb = make_float2(wv.z, wv.w);
+            acc[0][o4 / 2] = __ffma2_rn(wa, x0, acc[0][o4 / 2]);
+            acc[0][o4 / 2 + 1] = __ffma2_rn(wb, x0, acc[0][o4 / 2 + 1]);
+            acc[1][o4 / 2] = __ffma2_rn(wa, x1, acc[1][o4 / 2]);
+            acc[1][o4 / 2 + 1] = __ffma2_rn(wb, x1, acc[1][o4 / 2 + 1]);
         }
     }
     uint4* dst = h + (long long)img * G.plane * kPlanes;
@@ -641,8 +741,11 @@ cnn_first_kernel(const float* __restrict__ x, const float* __restrict__ w,
             uint32_t w4[4];
 #pragma unroll
             for (int hh = 0; hh < 4; ++hh) {
-                const int o = 8 * p + 2 * hh;
-                w4[hh] = inside[u] ? pack_bf16(fmaxf(acc[u][o], 0.0f), fmaxf(acc[u][o + 1], 0.0f)) : 0u;
+                // ReLU after rounding: rounding is monotone and keeps 0
+                const float2 a2 = acc[u][4 * p + hh];
+                const __nv_bfloat162 pk = __hmax2(__floats2bfloat162_rn(a2.x, a2.y),
+                                                  __floats2bfloat162_rn(0.0f, 0.0f));
+                w4[hh] = inside[u] ? *reinterpret_cast<const uint32_t*>(&pk) : 0u;
             }
             dst[r * kPlanes + chunk_pos(r, p)] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
         }
@@ -654,57 +757,6 @@ __device__ __forceinline__ void load_pixel32(float (&v)[kC], const uint4* recs, 
 {
 #pragma unroll
     for (int p = 0; p < kPlanes; ++p) unpack_record(recs[r * kPlanes + chunk_pos(r, p)], v + 8 * p);
-}
-
-// Last layer and the skip connection: y[p] = x[p] + b + sum_{tap, c} w[c][tap] h[p + off][c].
-// One 16 x 16 output tile per CTA: its 18 x 18 records (four chunks each) are staged in shared
-// memory once; the weights sit there as [tap][c] and reach registers as 16-byte broadcasts;
-// each thread sums the 9 taps x 32 channels of two pixels, rows ly and ly + 8 (pad records
-// are zero: no bounds tests).
-constexpr int kLT = 16;
-constexpr int kLH = kLT + 2;
-__global__ void __launch_bounds__(kLT * kLT / 2)
-cnn_last_kernel(const float* __restrict__ x, const uint4* __restrict__ h, const float* __restrict__ w,
-                float* __restrict__ y, int N)
-{
-    __shared__ __align__(16) float ws[kTaps][kC];
-    __shared__ uint4 hs[kPlanes][kLH * kLH];
-    for (int e = threadIdx.x; e < kC * kTaps; e += blockDim.x) ws[e % kTaps][e / kTaps] = w[e];
-    const float bias = w[kC * kTaps];
-    const ActGeom G = act_geom(N);
-    const int tiles_x = N / kLT;
-    const int y0 = (int)(blockIdx.x / tiles_x) * kLT, x0 = (int)(blockIdx.x % tiles_x) * kLT;
-    const uint4* hp = h + (long long)blockIdx.y * G.plane * kPlanes;
-    for (int e = threadIdx.x; e < kPlanes * kLH * kLH; e += blockDim.x) {
-        const int r = e / kPlanes, p = e - r * kPlanes;
-        const int ty = r / kLH, tx = r - ty * kLH;
-        const long long rec = rec_index(G, y0 - 1 + ty, x0 - 1 + tx);
-        hs[p][r] = hp[rec * kPlanes + chunk_pos(rec, p)];
-    }
-    __syncthreads();
-    const int ly = threadIdx.x / kLT, lx = threadIdx.x % kLT;      // rows ly and ly + 8
-    float s0 = bias, s1 = bias;
-    for (int tap = 0; tap < kTaps; ++tap) {
-        const int r = (ly + tap / 3) * kLH + lx + tap % 3;
-#pragma unroll
-        for (int p = 0; p < kPlanes; ++p) {
-            float v0[8], v1[8];
-            unpack_record(hs[p][r], v0);
-            unpack_record(hs[p][r + (kLT / 2) * kLH], v1);
-            const float4 wa = *reinterpret_cast<const float4*>(&ws[tap][8 * p]);
-            const float4 wb = *reinterpret_cast<const float4*>(&ws[tap][8 * p + 4]);
-            const float wk[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                s0 = fmaf(wk[e], v0[e], s0);
-                s1 = fmaf(wk[e], v1[e], s1);
-            }
-        }
-    }
-    const size_t pix = (size_t)blockIdx.y * N * N + (size_t)(y0 + ly) * N + x0 + lx;
-    y[pix] = x[pix] + s0;
-    const size_t pix1 = pix + (size_t)(kLT / 2) * N;
-    y[pix1] = x[pix1] + s1;
 }
 
 // Gradient through the last layer into the fifth layer's pre-activation:
@@ -870,11 +922,12 @@ size_t param_offset(int layer)
 
 size_t act_bytes(int N, int batch) { return (size_t)batch * kPlanes * act_geom(N).plane * 16; }
 
-// workspace: the weight images (4 layers x forward and transposed), then `nbuf` record
-// buffers (5 activations and 2 gradients when training, a ping-pong pair otherwise)
+// workspace: the weight images (4 layers x forward and transposed, and the last layer's),
+// then `nbuf` record buffers (5 activations and 2 gradients when training, a ping-pong pair
+// otherwise)
 size_t workspace_bytes(int N, int batch, int train)
 {
-    const size_t wbytes = (size_t)4 * 2 * kWBytes;
+    const size_t wbytes = (size_t)(4 * 2 + 1) * kWBytes;
     const int nbuf = train ? 5 + 2 : 2;
     return wbytes + (size_t)nbuf * act_bytes(N, batch);
 }
@@ -882,6 +935,7 @@ size_t workspace_bytes(int N, int batch, int train)
 struct Ws {
     bf16* wf[4];
     bf16* wb[4];
+    bf16* wl;
     uint4* act[7];
 };
 
@@ -891,6 +945,8 @@ Ws carve(void* ws, int N, int batch, int train)
     unsigned char* p = static_cast<unsigned char*>(ws);
     for (int k = 0; k < 4; ++k) { w.wf[k] = reinterpret_cast<bf16*>(p); p += kWBytes; }
     for (int k = 0; k < 4; ++k) { w.wb[k] = reinterpret_cast<bf16*>(p); p += kWBytes; }
+    w.wl = reinterpret_cast<bf16*>(p);
+    p += kWBytes;
     const size_t a = act_bytes(N, batch);
     for (int k = 0; k < (train ? 7 : 2); ++k) { w.act[k] = reinterpret_cast<uint4*>(p); p += a; }
     return w;
@@ -898,9 +954,10 @@ Ws carve(void* ws, int N, int batch, int train)
 
 constexpr int kMaxCnnDevices = 64;
 
-template <bool BIAS, bool RELU, bool MASK>
+template <bool BIAS, bool RELU, bool MASK, bool LAST = false>
 cudaError_t launch_conv32(const uint4* in, const bf16* wt, const float* bias, const uint4* mask,
-                          uint4* out, int N, int batch, int sms, cudaStream_t st)
+                          uint4* out, int N, int batch, int sms, cudaStream_t st,
+                          const float* ximg = nullptr, float* yimg = nullptr)
 {
     // the shared-memory opt-in is per device: done once for each device this runs on
     static std::mutex lock;
@@ -912,7 +969,7 @@ cudaError_t launch_conv32(const uint4* in, const bf16* wt, const float* bias, co
     {
         std::lock_guard<std::mutex> g(lock);
         if (!done[dev]) {
-            e = cudaFuncSetAttribute(cnn_conv32_kernel<BIAS, RELU, MASK>,
+            e = cudaFuncSetAttribute(cnn_conv32_kernel<BIAS, RELU, MASK, LAST>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConvSmem);
             if (e != cudaSuccess) return e;
             done[dev] = true;
@@ -920,8 +977,8 @@ cudaError_t launch_conv32(const uint4* in, const bf16* wt, const float* bias, co
     }
     const long long tiles = (long long)act_geom(N).T * batch;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    ConvArgs a{in, wt, bias, mask, out, N, batch};
-    cnn_conv32_kernel<BIAS, RELU, MASK><<<grid, kConvThreads, kConvSmem, st>>>(a);
+    ConvArgs a{in, wt, bias, mask, out, ximg, yimg, N, batch};
+    cnn_conv32_kernel<BIAS, RELU, MASK, LAST><<<grid, kConvThreads, kConvSmem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -943,7 +1000,6 @@ cudaError_t forward(const float* params, const float* x, float* y, void* ws, int
             params + param_offset(k + 1), w.wf[k], w.wb[k]);
     const ActGeom G = act_geom(N);
     const dim3 fg((unsigned)((G.plane + 2 * kFirstStride - 1) / (2 * kFirstStride)), batch);
-    const dim3 lg((N / kLT) * (N / kLT), batch);
     // h1 .. h5 in act[0..4] when saving for the backward pass, else ping-pong in act[0..1]
     auto hbuf = [&](int k) { return save ? w.act[k] : w.act[k & 1]; };
     cnn_first_kernel<<<fg, 128, 0, st>>>(x, params, hbuf(0), N);
@@ -955,8 +1011,9 @@ cudaError_t forward(const float* params, const float* x, float* y, void* ws, int
                                                                nullptr, hbuf(k), N, batch, sms, st);
         if (e != cudaSuccess) return e;
     }
-    cnn_last_kernel<<<lg, kLT * kLT / 2, 0, st>>>(x, hbuf(4), params + param_offset(5), y, N);
-    return cudaGetLastError();
+    cnn_prep_last_kernel<<<(kWChunks * kWRows * 8 + 255) / 256, 256, 0, st>>>(params + param_offset(5), w.wl);
+    return launch_conv32<false, false, false, true>(hbuf(4), w.wl, params + param_offset(5) + kC * kTaps,
+                                                    nullptr, nullptr, N, batch, sms, st, x, y);
 }
 
 cudaError_t backward(const float* params, const float* x, const float* gy, float* gparams,
