@@ -678,78 +678,121 @@ cnn_conv32_kernel(ConvArgs a)
 
 // ---------------------------------------------------------------- 1 -> 32 and 32 -> 1
 // First layer: h[p][o] = relu(b[o] + sum_tap w[o][tap] x[p + off(tap)]), fp32 math, written
-// as records over the whole plane (zero outside the image).  The weights sit in shared
-// memory as [tap][o] and reach registers as 16-byte broadcasts, 32 per tap; each thread
-// computes the records r and r + kFirstStride, two output channels per packed fp32 FMA
-// (each channel's sum is the same chain of fmaf as one at a time).
-constexpr int kFirstStride = 128;           // records between a thread's two records
-__global__ void __launch_bounds__(128)
+// as records over the whole plane (zero outside the image).  CTA (row segment, row y,
+// image); thread = 4 consecutive pixels x0 .. x0+3 of row y, whose 3 x 6 input window it
+// loads once (a 16-byte load and two single values per row).  The weights sit in shared
+// memory as [tap][o] and reach registers as 16-byte broadcasts; the 32 channels go in four
+// passes of 8 (one record chunk each), two channels per packed fp32 FMA (each channel's sum
+// is the same chain of fmaf, bias first and taps in order, as one at a time).  The
+// segment's records are assembled in shared memory (a thread's 4 records, then 16 bytes of
+// padding, so that the 16-byte writes of a warp fall in distinct banks) and leave as whole
+// records in consecutive 16-byte stores.  The row's pad records (x = -1, x = N) are written
+// by its first and last threads; grid row y = N zeroes the guard, the top and bottom pad
+// rows and the tail.
+constexpr int kFirstThreads = 128;
+constexpr int kFirstPx = 4;                  // pixels per thread
+constexpr int kFirstStage = kFirstPx * kPlanes + 1;        // 16-byte words per thread in shared memory
+__global__ void __launch_bounds__(kFirstThreads)
 cnn_first_kernel(const float* __restrict__ x, const float* __restrict__ w,
                  uint4* __restrict__ h, int N)
 {
     __shared__ __align__(16) float ws[kTaps][kC];
     __shared__ float bs[kC];
+    __shared__ uint4 stage[kFirstThreads * kFirstStage];
     for (int e = threadIdx.x; e < kC * kTaps; e += blockDim.x) ws[e % kTaps][e / kTaps] = w[e];
     for (int e = threadIdx.x; e < kC; e += blockDim.x) bs[e] = w[kC * kTaps + e];
-    __syncthreads();
     const ActGeom G = act_geom(N);
-    const long long r0 = (long long)blockIdx.x * 2 * kFirstStride + threadIdx.x;
-    const int img = blockIdx.y;
-    const float* xs = x + (size_t)img * N * N;
-    float v[2][kTaps];
-    bool inside[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const long long r = r0 + u * kFirstStride;
-        int py = -2, px = -2;                   // pixel of record r (32-bit: r < 2^31)
-        if (r >= kRecGuard && r < G.plane) {
-            const unsigned q = (unsigned)(r - kRecGuard);
-            const unsigned yy = q / (unsigned)G.W;
-            py = (int)yy - 1;
-            px = (int)(q - yy * (unsigned)G.W) - 1;
+    const int y = blockIdx.y, img = blockIdx.z;
+    uint4* dst = h + (long long)img * G.plane * kPlanes;
+    const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
+    if (y == N) {
+        // records outside every image row: [0, kRecGuard + W) and [kRecGuard + (N+1) W, plane)
+        const long long head = kRecGuard + G.W;
+        const long long tail0 = kRecGuard + (long long)(N + 1) * G.W;
+        const long long n = (head + G.plane - tail0) * kPlanes;
+        for (long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x; z < n;
+             z += (long long)gridDim.x * blockDim.x) {
+            const long long r = z / kPlanes;
+            dst[(r < head ? r : tail0 + (r - head)) * kPlanes + (int)(z - r * kPlanes)] = zero4;
         }
-        inside[u] = (unsigned)py < (unsigned)N && (unsigned)px < (unsigned)N;
+        return;
+    }
+    __syncthreads();
+    const int x0 = kFirstPx * (blockIdx.x * kFirstThreads + threadIdx.x);
+    const long long rrow = rec_index(G, y, 0);               // record of pixel (y, 0)
+    if (x0 == 0)
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) dst[(rrow - 1) * kPlanes + p] = zero4;
+    if (x0 + kFirstPx == N)
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) dst[(rrow + N) * kPlanes + p] = zero4;
+    const bool live = x0 < N;
+    uint4* mine = stage + threadIdx.x * kFirstStage;
+    // window xv[dy][k] = x(y + dy - 1, x0 + k - 1), k = 0..5, zero outside the image
+    const float* xs = x + (size_t)img * N * N;
+    float xv[3][kFirstPx + 2];
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) {
+        const int yy = y + dy - 1;
+        if (live && (unsigned)yy < (unsigned)N) {
+            const float* row = xs + (size_t)yy * N;
+            const float4 mid = *reinterpret_cast<const float4*>(row + x0);
+            xv[dy][0] = x0 > 0 ? row[x0 - 1] : 0.0f;
+            xv[dy][1] = mid.x;
+            xv[dy][2] = mid.y;
+            xv[dy][3] = mid.z;
+            xv[dy][4] = mid.w;
+            xv[dy][5] = x0 + kFirstPx < N ? row[x0 + kFirstPx] : 0.0f;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kFirstPx + 2; ++k) xv[dy][k] = 0.0f;
+        }
+    }
+#pragma unroll 1
+    for (int c = 0; c < kPlanes; ++c) {                       // channels 8c .. 8c + 7
+        float2 acc[kFirstPx][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float2 b2 = make_float2(bs[8 * c + 2 * k], bs[8 * c + 2 * k + 1]);
+#pragma unroll
+            for (int u = 0; u < kFirstPx; ++u) acc[u][k] = b2;
+        }
 #pragma unroll
         for (int tap = 0; tap < kTaps; ++tap) {
-            const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
-            v[u][tap] = (inside[u] && yy >= 0 && yy < N && xx >= 0 && xx < N) ? xs[(size_t)yy * N + xx] : 0.0f;
+            const int dy = tap / 3, dx = tap % 3;
+            const float4 wa = *reinterpret_cast<const float4*>(&ws[tap][8 * c]);
+            const float4 wb = *reinterpret_cast<const float4*>(&ws[tap][8 * c + 4]);
+            const float2 wk[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w),
+                                  make_float2(wb.x, wb.y), make_float2(wb.z, wb.w)};
+#pragma unroll
+            for (int u = 0; u < kFirstPx; ++u) {
+                const float v = xv[dy][u + dx];
+                const float2 v2 = make_float2(v, v);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[u][k] = __ffma2_rn(wk[k], v2, acc[u][k]);
+            }
         }
-    }
-    float2 acc[2][kC / 2];                      // channels (2k, 2k + 1)
 #pragma unroll
-    for (int k = 0; k < kC / 2; ++k) acc[0][k] = acc[1][k] = make_float2(bs[2 * k], bs[2 * k + 1]);
-#pragma unroll
-    for (int tap = 0; tap < kTaps; ++tap) {
-        const float2 x0 = make_float2(v[0][tap], v[0][tap]), x1 = make_float2(v[1][tap], v[1][tap]);
-#pragma unroll
-        for (int o4 = 0; o4 < kC; o4 += 4) {
-            const float4 wv = *reinterpret_cast<const float4*>(&ws[tap][o4]);
-            const float2 wa = make_float2(wv.x, wv.y), wb = make_float2(wv.z, wv.w);
-            acc[0][o4 / 2] = __ffma2_rn(wa, x0, acc[0][o4 / 2]);
-            acc[0][o4 / 2 + 1] = __ffma2_rn(wb, x0, acc[0][o4 / 2 + 1]);
-            acc[1][o4 / 2] = __ffma2_rn(wa, x1, acc[1][o4 / 2]);
-            acc[1][o4 / 2 + 1] = __ffma2_rn(wb, x1, acc[1][o4 / 2 + 1]);
-        }
-    }
-    uint4* dst = h + (long long)img * G.plane * kPlanes;
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        const long long r = r0 + u * kFirstStride;
-        if (r >= G.plane) continue;
-#pragma unroll
-        for (int p = 0; p < kPlanes; ++p) {
+        for (int u = 0; u < kFirstPx; ++u) {
+            const long long r = rrow + x0 + u;
             uint32_t w4[4];
 #pragma unroll
             for (int hh = 0; hh < 4; ++hh) {
                 // ReLU after rounding: rounding is monotone and keeps 0
-                const float2 a2 = acc[u][4 * p + hh];
-                const __nv_bfloat162 pk = __hmax2(__floats2bfloat162_rn(a2.x, a2.y),
+                const __nv_bfloat162 pk = __hmax2(__floats2bfloat162_rn(acc[u][hh].x, acc[u][hh].y),
                                                   __floats2bfloat162_rn(0.0f, 0.0f));
-                w4[hh] = inside[u] ? *reinterpret_cast<const uint32_t*>(&pk) : 0u;
+                w4[hh] = *reinterpret_cast<const uint32_t*>(&pk);
             }
-            dst[r * kPlanes + chunk_pos(r, p)] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            mine[u * kPlanes + chunk_pos(r, c)] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
         }
     }
+    __syncthreads();
+    // the segment's records, whole, in consecutive 16-byte words
+    const int sx0 = kFirstPx * blockIdx.x * kFirstThreads;   // the segment's first pixel
+    const int nw = min(N - sx0, kFirstPx * kFirstThreads) * kPlanes;
+    uint4* out = dst + (rrow + sx0) * kPlanes;
+    for (int e = threadIdx.x; e < nw; e += kFirstThreads)
+        out[e] = stage[(e / (kFirstPx * kPlanes)) * kFirstStage + e % (kFirstPx * kPlanes)];
 }
 
 // the 32 channels of record r of one image's records
@@ -999,10 +1042,10 @@ cudaError_t forward(const float* params, const float* x, float* y, void* ws, int
         cnn_prep_weights_kernel<<<(kWChunks * kWRows * 8 + 255) / 256, 256, 0, st>>>(
             params + param_offset(k + 1), w.wf[k], w.wb[k]);
     const ActGeom G = act_geom(N);
-    const dim3 fg((unsigned)((G.plane + 2 * kFirstStride - 1) / (2 * kFirstStride)), batch);
+    const dim3 fg((unsigned)((N + kFirstPx * kFirstThreads - 1) / (kFirstPx * kFirstThreads)), N + 1, batch);
     // h1 .. h5 in act[0..4] when saving for the backward pass, else ping-pong in act[0..1]
     auto hbuf = [&](int k) { return save ? w.act[k] : w.act[k & 1]; };
-    cnn_first_kernel<<<fg, 128, 0, st>>>(x, params, hbuf(0), N);
+    cnn_first_kernel<<<fg, kFirstThreads, 0, st>>>(x, params, hbuf(0), N);
     const int sms = device_sms();
     if (sms <= 0) return cudaErrorInvalidDevice;
     for (int k = 1; k <= 4; ++k) {
