@@ -936,6 +936,83 @@ cnn_wgrad_kernel(const void* __restrict__ gz_, const void* __restrict__ hp_, flo
     if (tid < CO) atomicAdd(gb + tid, accb);
 }
 
+// Weight gradient of a 32 -> 32 layer, the same sums as cnn_wgrad_kernel<32, 32> with the
+// work laid out for registers: per 8 x 16-pixel tile the gradient gz (128 pixels) and the
+// layer input hp (its 10 x 18-pixel halo) are unpacked to fp32 in shared memory; thread
+// (tap, ob, cb) owns the 4 x 4 block o = 4ob .. 4ob+3, c = 4cb .. 4cb+3 of one tap and
+// sweeps the tile's pixels, two channels per packed FMA.  A warp holds one tap and 4 x 8
+// blocks, so its 16-byte shared loads read 4 (gz) and 8 (hp) distinct addresses.  Threads
+// 0..31 sum the bias gradient of their channel.  Persistent CTAs add into gw and gb once.
+constexpr int kWg32Threads = kTaps * 64;
+__global__ void __launch_bounds__(kWg32Threads, 2)
+cnn_wgrad32_kernel(const uint4* __restrict__ gz, const uint4* __restrict__ hp, float* __restrict__ gw,
+                   float* __restrict__ gb, int N, int images)
+{
+    __shared__ __align__(16) float gzs[kTileY * kTileX][kC];
+    __shared__ __align__(16) float hps[kHaloY * kHaloX][kC];
+    const ActGeom G = act_geom(N);
+    const int tid = threadIdx.x;
+    const int tap = tid >> 6, ob = (tid >> 3) & 7, cb = tid & 7;
+    const int dy = tap / 3, dx = tap % 3;
+    float2 acc[4][2];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k][0] = acc[k][1] = make_float2(0.0f, 0.0f);
+    float accb = 0.0f;
+    const int tiles_x = N / kTileX, tiles_y = N / kTileY;
+    const long long tiles = (long long)tiles_x * tiles_y * images;
+    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int im = (int)(tile / ((long long)tiles_x * tiles_y));
+        const int rem = (int)(tile - (long long)im * tiles_x * tiles_y);
+        const int y0 = (rem / tiles_x) * kTileY, x0 = (rem % tiles_x) * kTileX;
+        const uint4* gzi = gz + (long long)im * G.plane * kPlanes;
+        const uint4* hpi = hp + (long long)im * G.plane * kPlanes;
+        __syncthreads();                               // previous tile consumed
+        for (int e = tid; e < kTileY * kTileX * kPlanes; e += kWg32Threads) {
+            const int pix = e / kPlanes, ch = e - pix * kPlanes;
+            const long long r = rec_index(G, y0 + pix / kTileX, x0 + pix % kTileX);
+            float v[8];
+            unpack_record(gzi[r * kPlanes + chunk_pos(r, ch)], v);
+            *reinterpret_cast<float4*>(&gzs[pix][8 * ch]) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4*>(&gzs[pix][8 * ch + 4]) = make_float4(v[4], v[5], v[6], v[7]);
+        }
+        for (int e = tid; e < kHaloY * kHaloX * kPlanes; e += kWg32Threads) {
+            const int pix = e / kPlanes, ch = e - pix * kPlanes;
+            const long long r = rec_index(G, y0 - 1 + pix / kHaloX, x0 - 1 + pix % kHaloX);
+            float v[8];
+            unpack_record(hpi[r * kPlanes + chunk_pos(r, ch)], v);
+            *reinterpret_cast<float4*>(&hps[pix][8 * ch]) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4*>(&hps[pix][8 * ch + 4]) = make_float4(v[4], v[5], v[6], v[7]);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int p = 0; p < kTileY * kTileX; ++p) {
+            const int py = p / kTileX, px = p % kTileX;
+            const float4 g4 = *reinterpret_cast<const float4*>(&gzs[p][4 * ob]);
+            const float4 h4 = *reinterpret_cast<const float4*>(&hps[(py + dy) * kHaloX + px + dx][4 * cb]);
+            const float2 h01 = make_float2(h4.x, h4.y), h23 = make_float2(h4.z, h4.w);
+            const float gk[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float2 g2 = make_float2(gk[k], gk[k]);
+                acc[k][0] = __ffma2_rn(g2, h01, acc[k][0]);
+                acc[k][1] = __ffma2_rn(g2, h23, acc[k][1]);
+            }
+        }
+        if (tid < kC)
+            for (int p = 0; p < kTileY * kTileX; ++p) accb += gzs[p][tid];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int o = 4 * ob + k;
+        float* dst = gw + ((size_t)o * kC + 4 * cb) * kTaps + tap;
+        atomicAdd(dst, acc[k][0].x);
+        atomicAdd(dst + kTaps, acc[k][0].y);
+        atomicAdd(dst + 2 * kTaps, acc[k][1].x);
+        atomicAdd(dst + 3 * kTaps, acc[k][1].y);
+    }
+    if (tid < kC) atomicAdd(gb + tid, accb);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- host side
@@ -1077,8 +1154,8 @@ cudaError_t backward(const float* params, const float* x, const float* gy, float
     // layers 5 .. 2 (32 -> 32): weights from h_{k-1} and g_z_k; gradient into z_{k-1}
     for (int k = 4; k >= 1; --k) {
         gw = gparams + param_offset(k);
-        cnn_wgrad_kernel<kC, kC><<<wgrid, 256, 0, st>>>(g[cur], w.act[k - 1], gw,
-                                                        gw + kC * kC * kTaps, N, batch);
+        cnn_wgrad32_kernel<<<wgrid, kWg32Threads, 0, st>>>(g[cur], w.act[k - 1], gw,
+                                                           gw + kC * kC * kTaps, N, batch);
         e = launch_conv32<false, false, true>(g[cur], w.wb[k - 1], nullptr, w.act[k - 1],
                                               g[cur ^ 1], N, batch, sms, st);
         if (e != cudaSuccess) return e;
