@@ -145,12 +145,15 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// One bounded wait for the phase: the thread may sleep up to kSuspendNs inside the try
+// (instead of spinning through issue slots) and returns whether the phase has completed.
+constexpr unsigned kSuspendNs = 100000;
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
 {
     uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
                  " selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity), "n"(kSuspendNs) : "memory");
     return ok != 0;
 }
 
