@@ -91,6 +91,48 @@ def test_integer_network_bit_exact_over_many_tiles(fbp, torch):
     assert bad.size == 0, f"{bad.size} parameter gradients differ, first at {bad[:8]}"
 
 
+@pytest.mark.parametrize("N,B", [(16, 3), (32, 1), (64, 2)])
+def test_integer_network_bit_exact_smallest_sizes(fbp, torch, N, B):
+    """The smallest images: 2 to 17 tensor-core tiles per image, first-layer rows of 4 to 16
+    threads, pad records at both ends of every row handled by the same threads."""
+    rng = np.random.default_rng(100 + N)
+    ps = int_params(5)
+    x = int_images(rng, (B, N, N), 0.7)
+    gy = int_images(rng, (B, N, N), 0.5)
+    y, g = run_gpu(fbp, torch, flatten(ps), x, gy)
+    want_g = np.zeros(g.size)
+    for b in range(B):
+        yb, cache = ocnn.forward(ps, x[b], "bf16")
+        assert np.array_equal(y[b], yb), f"N={N} image {b}: forward differs"
+        grads, _ = ocnn.backward(ps, cache, gy[b], "bf16")
+        want_g += flatten(grads).astype(np.float64)
+    assert np.array_equal(g, want_g)
+
+
+def test_last_layer_weight_split_is_exact(fbp, torch):
+    """The 32 -> 1 layer multiplies its float32 weights on the tensor cores as three bfloat16
+    parts (hi + mid + lo).  Hidden layers with zero weights and bias 1 make every hidden
+    activation 1 inside the image; two last-layer weights need all three parts
+    (1 + 2^-9 + 2^-18: hi = 1, mid = 2^-9, lo = 2^-18), and every partial sum of the output
+    stays within 22 significant bits, so the output must equal the float64 network exactly.
+    Dropping a part, or rounding a weight to bfloat16, moves it."""
+    N, B = 64, 2
+    ps = [(np.zeros((32, 1, 3, 3)), np.ones(32))]
+    ps += [(np.zeros((32, 32, 3, 3)), np.ones(32)) for _ in range(4)]
+    w6 = np.zeros((1, 32, 3, 3))
+    w6[0, 0, 1, 1] = 1.0 + 2.0 ** -9 + 2.0 ** -18
+    w6[0, 5, 0, 2] = 2.0 ** -3 + 2.0 ** -12 + 2.0 ** -20
+    ps.append((w6, np.array([0.25])))
+    rng = np.random.default_rng(7)
+    x = rng.integers(-3, 4, size=(B, N, N)).astype(np.float64)
+    y, _ = run_gpu(fbp, torch, flatten(ps), x)
+    for b in range(B):
+        want, _ = ocnn.forward(ps, x[b], "f64")
+        assert np.array_equal(y[b], want), float(np.abs(y[b] - want).max())
+    # the float32 weights are what the library was given
+    assert float(np.float32(w6[0, 0, 1, 1])) == w6[0, 0, 1, 1]
+
+
 def random_params(seed, rng):
     from paper_2007_06289_gb300 import corrector
     flat = corrector.init_params(seed=seed, scale=2.0)
