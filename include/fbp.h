@@ -364,9 +364,10 @@ const char* fbp_status_str(fbp_status status);
  * FBP_ERR_INTERNAL when a kernel rejected a geometry-table row naming an angle row outside
  * the sinogram (checked in every build; the row is resampled as zeros) or, in the library
  * built with FBP_BOUNDS_CHECK (libfbp_checked.so, include/fbp_check.h), an index outside its
- * buffer or Hough tile (the access is skipped); FBP_OK if none since the last read.  The
- * plan's kernels never wait on one another, so FBP_ERR_TIMEOUT does not occur here (the
- * corrector's bounded waits report through fbp_cnn_last_error). */
+ * buffer or Hough tile (the access is skipped); FBP_ERR_TIMEOUT when a second-pass CTA gave
+ * up its bounded wait (about a second) for its bulk row copies (its output tile is then
+ * wrong); FBP_OK if none since the last read.  The corrector's bounded waits report through
+ * fbp_cnn_last_error. */
 fbp_status fbp_last_device_error(fbp_plan_t plan);
 
 #ifdef __cplusplus

@@ -628,13 +628,67 @@ __device__ __forceinline__ void cp_async_wait_group()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N_PENDING) : "memory");
 }
 
+// Whole G rows of the second pass arrive by 1-D bulk copies counted on an mbarrier: every
+// issuing lane adds its bytes to the barrier's transaction count before its copy, and one
+// thread arrives once all have (after a CTA barrier), so the phase completes when the last
+// copy has landed.
+__device__ __forceinline__ unsigned smem_addr(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect(uint64_t* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bulk_row(float* dst, const float* src, unsigned bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+// Waits for phase 0 of `bar`, for at most about a second (then sets FBP_ERR_TIMEOUT in the
+// status word and returns: the copies are lost, nothing hangs).
+__device__ __forceinline__ void bar_wait(uint64_t* bar, int* status)
+{
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
+        unsigned ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+                     " selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(ok) : "r"(smem_addr(bar)) : "memory");
+        if (ok) return;
+        unsigned long long now;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+        if (it == 0) t0 = now;
+        else if (now - t0 > 1000000000ull) {
+            flag_status(status, (int)FBP_ERR_TIMEOUT);
+            return;
+        }
+    }
+}
+
 // CTA = (tile of T2 intercepts u, slope group tau_hi, slice).  Runs the second pass for the
 // '-' quarter on u in [x0, x0+T2) and for the '+' quarter on the mirrored range, adds them
 // (F_- + F_+), and either stores the sum into the image (v quarters: [y = tau][x = u]) or
 // adds it to the image through a shared-memory transpose (h quarters: [y = u][x = tau]).
 // Launched for the v quarters first and the h quarters second, so each pixel ends as
-// (F_v- + F_v+) + (F_h- + F_h+).  Both quarters' rows are requested up front (one copy
-// group each), so the second quarter's copies run behind the first quarter's stages.
+// (F_v- + F_v+) + (F_h- + F_h+).  Both quarters' rows are requested up front (one bulk
+// copy per row that lies wholly inside its stored range, counted on the quarter's mbarrier;
+// 16-byte asynchronous copies with zero fill for the rows at the ends of the range), so the
+// second quarter's copies run behind the first quarter's stages.
 template <int LOGR2, int T2, bool HORIZ>
 __global__ void __launch_bounds__(kNT2, 3)
 pass2_kernel(Pass2Args a)
@@ -659,6 +713,13 @@ pass2_kernel(Pass2Args a)
     float* img = a.img_tab ? a.img_tab[s] : a.img + (size_t)s * N * N;
     const Span gs{a.g, a.g_n, a.status};
     const Span is{img, (long long)N * N, a.status};    // this slice's image
+    __shared__ uint64_t rows_landed[2];                // per quarter: its bulk row copies
+    if (threadIdx.x == 0) {
+        bar_init(&rows_landed[0]);
+        bar_init(&rows_landed[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
 
 #pragma unroll 1
     for (int half = 0; half < 2; ++half) {
@@ -678,6 +739,14 @@ pass2_kernel(Pass2Args a)
             const int sb = uo + tau_hi * ih + sh;
             const float* grow = gq + ((size_t)ih * R1 + tau_hi) * W;
             float* drow = hb + ih * PITCH;
+            if (sb >= lo && sb + WB <= hi && gs.ok(grow + sb) && gs.ok(grow + sb + WB - 1)) {
+                if (lane == 0) {
+                    bar_expect(&rows_landed[half], WB * 4);
+                    bulk_row(drow, grow + sb, WB * 4, &rows_landed[half]);
+                }
+                for (int p = WB + lane; p < PITCH; p += 32) drow[p] = 0.0f;
+                continue;
+            }
 #pragma unroll
             for (int m = lane; m < WB / 4; m += 32) {
                 const int st = sb + 4 * m;
@@ -697,10 +766,17 @@ pass2_kernel(Pass2Args a)
         }
         cp_async_commit();
     }
+    __syncthreads();                                   // every bulk copy is counted
+    if (threadIdx.x == 0) {
+        bar_arrive(&rows_landed[0]);
+        bar_arrive(&rows_landed[1]);
+    }
     cp_async_wait_group<1>();
+    bar_wait(&rows_landed[0], a.status);
     __syncthreads();
     hough_stages<LOGR2, WB, PITCH, NWARPS>(hb0, warp, lane, SmemSink{}, a.status);
     cp_async_wait_group<0>();
+    bar_wait(&rows_landed[1], a.status);
     __syncthreads();
     hough_stages<LOGR2, WB, PITCH, NWARPS>(hb1, warp, lane, SmemSink{}, a.status);
 
