@@ -741,7 +741,9 @@ def run_corrector(args):
     direct FBP (--sample-pixels pixels of slice 0, CPU oracle) of the fast reconstruction with
     the default filter table, with the table fitted against the direct FBP, with the paper's
     impulse-response-MSE fit, with the exact FIR filter (which isolates the dyadic lines'
-    share of the error), the corrected fast reconstruction and the direct GPU FBP.  The
+    share of the error), the corrected fast reconstructions (one corrector trained on the
+    order-3 images, one on the order-6 images, both against the direct FBP) and the direct GPU
+    FBP.  The
     dominant kernel is the bf16 tensor-core 3x3 convolution (5 of the 6 layers: the four
     32 -> 32 layers and the 32 -> 1 layer)."""
     import numpy as np
@@ -767,10 +769,13 @@ def run_corrector(args):
     t0 = time.perf_counter()
     Nt, P, held = 512, args.train_pairs, 32
     Kt, Mt = phantoms.geometry_for(Nt)
-    fast512 = torch.empty(P + held, Nt, Nt, device=dev)
+    fast512 = torch.empty(P + held, Nt, Nt, device=dev)          # order-3 filter (the paper's)
+    fast512_6 = torch.empty(P + held, Nt, Nt, device=dev)        # order-6 filter
     direct512 = torch.empty(P + held, Nt, Nt, device=dev)
     chunk = 500
     fplan = fbp.fbp_plan(Nt, Kt, Mt, chunk)
+    b6, a6 = iir_fit.coefficients(Nt, 6)
+    fplan6 = fbp.fbp_plan(Nt, Kt, Mt, chunk, (list(b6), list(a6)))
     dplan = fbp.fbp_plan(Nt, Kt, Mt, chunk)
     for c0 in range(0, P + held, chunk):
         n = min(chunk, P + held - c0)
@@ -778,21 +783,28 @@ def run_corrector(args):
         fout = torch.empty(chunk, Nt, Nt, device=dev)
         dout = torch.empty(chunk, Nt, Nt, device=dev)
         fbp.fbp_reconstruct(fplan, sino, fout)
-        fbp.fbp_direct_reconstruct(dplan, sino, dout)
         fast512[c0:c0 + n] = fout[:n]
+        fbp.fbp_reconstruct(fplan6, sino, fout)
+        fast512_6[c0:c0 + n] = fout[:n]
+        fbp.fbp_direct_reconstruct(dplan, sino, dout)
         direct512[c0:c0 + n] = dout[:n]
     torch.cuda.synchronize(dev)
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     params, losses = corrector.train(fast512[:P], direct512[:P], steps=args.train_steps, batch=16,
                                      lr=2e-3, seed=0)
+    params6, losses6 = corrector.train(fast512_6[:P], direct512[:P], steps=args.train_steps,
+                                       batch=16, lr=2e-3, seed=0)
     torch.cuda.synchronize(dev)
     train_s = time.perf_counter() - t0
     hs = slice(P, P + held)
     q512 = {"rmse_fast_vs_direct": rmse(fast512[hs], direct512[hs]),
             "rmse_corrected_vs_direct": rmse(corrector.infer(params, fast512[hs].contiguous()),
-                                              direct512[hs])}
-    del fast512, direct512
+                                              direct512[hs]),
+            "rmse_fast_order6_vs_direct": rmse(fast512_6[hs], direct512[hs]),
+            "rmse_corrected_order6_vs_direct": rmse(corrector.infer(params6, fast512_6[hs].contiguous()),
+                                                     direct512[hs])}
+    del fast512, fast512_6, direct512
 
     # ---- the forms at N = 2048
     N, B = 2048, min(16, args.slices)
@@ -829,6 +841,8 @@ def run_corrector(args):
     ws = torch.empty(fbp.fbp_cnn_workspace_bytes(N, B, False), dtype=torch.uint8, device=dev)
     corrected = torch.empty(B, N, N, device=dev)
     fbp.fbp_cnn_forward(params, imgs["fast"], corrected, ws)
+    corrected6 = torch.empty(B, N, N, device=dev)
+    fbp.fbp_cnn_forward(params6, imgs["fast_order6"], corrected6, ws)
     direct = torch.empty(D, N, N, device=dev)
     dplan2 = fbp.fbp_plan(N, K, M, D)
     fbp.fbp_direct_reconstruct(dplan2, sino[:D].contiguous(), direct)
@@ -887,11 +901,14 @@ def run_corrector(args):
     quality = {k: q(v) for k, v in imgs.items()}
     quality["fast_exact_fir_filter"] = q(fir_fast)
     quality["corrected"] = q(corrected)
+    quality["corrected_order6"] = q(corrected6)
     quality["direct_gpu"] = q(direct)
     sps = lambda ms, n: round(n * world / (ms / 1e3), 2)
     throughput = {k: sps(v, B) for k, v in ms_form.items()}
     throughput.update({"fast_exact_fir_filter": sps(ms_fir, B),
-                       "corrected": sps(ms_fast + ms_inf, B), "direct_gpu": sps(ms_direct, D)})
+                       "corrected": sps(ms_fast + ms_inf, B),
+                       "corrected_order6": sps(ms_form["fast_order6"] + ms_inf, B),
+                       "direct_gpu": sps(ms_direct, D)})
     flops_px = 2 * (32 * 9) + 4 * 2 * (32 * 32 * 9) + 2 * (32 * 9)
     tflops = B * N * N * flops_px / (ms_inf / 1e3) / 1e12
     peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -916,6 +933,7 @@ def run_corrector(args):
             "throughput_N2048_slices_per_s": throughput,
             "quality_N512_held_out_32": q512,
             "training": {"loss_first_last": [round(losses[0], 6), round(losses[-1], 6)],
+                         "loss_first_last_order6": [round(losses6[0], 6), round(losses6[-1], 6)],
                          "pair_generation_seconds": round(gen_s, 1),
                          "train_seconds": round(train_s, 1)},
             "training_step_ms_N2048_batch4": round(ms_train, 3),
