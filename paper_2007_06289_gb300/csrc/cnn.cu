@@ -861,86 +861,85 @@ cnn_last_backward_kernel(const float* __restrict__ gy, const uint4* __restrict__
 
 // ---------------------------------------------------------------- weight gradients (fp32)
 // gw[o][c][tap] += sum_p gz[p][o] hp[p + off(tap)][c], gb[o] += sum_p gz[p][o], over all pixels
-// of all images.  CO / CI are 32 or 1; a 1-channel operand is fp32 [N][N] (the image or the
-// output gradient), a 32-channel one records.  Persistent CTAs accumulate over 8 x 16-pixel
-// tiles in registers and add once into the global gradient.
-__device__ __forceinline__ float record_channel(const uint4* recs, long long r, int c)
+// of all images.  Persistent CTAs accumulate over 8 x 16-pixel tiles in registers and add
+// once into the global gradient (float atomics: the last bits depend on the order).
+// Weight gradients of the two 1-channel layers.  Each has a wide side (32 channels, records) and a thin
+// side (one channel, an fp32 image); gw[ch][tap] (ch the wide side's channel) sums wide x thin
+// over the pixels, one of the two taken at the tap's offset.  WIDE_IS_GZ: first layer, wide =
+// the pre-activation gradient gz (unshifted), thin = the input image x (shifted); else last
+// layer, wide = the layer's input h (shifted), thin = the output gradient gy (unshifted).
+// Per 8 x 16-pixel tile both sides are staged as fp32 in shared memory; thread (group, tap,
+// cb) owns channels 4cb .. 4cb+3 of one tap over every fourth pixel of the tile (group =
+// pixel mod 4), so each pixel costs one 16-byte and one broadcast shared load for 4 FMAs.
+constexpr int kWgThinThreads = 4 * kTaps * 8;
+template <bool WIDE_IS_GZ>
+__global__ void __launch_bounds__(kWgThinThreads)
+cnn_wgrad_thin_kernel(const uint4* __restrict__ wide, const float* __restrict__ thin,
+                      float* __restrict__ gw, float* __restrict__ gb, int N, int images)
 {
-    const bf16* rec = reinterpret_cast<const bf16*>(recs + r * kPlanes + chunk_pos(r, c >> 3));
-    return __bfloat162float(rec[c & 7]);
-}
-
-template <int CO, int CI>
-__global__ void __launch_bounds__(256)
-cnn_wgrad_kernel(const void* __restrict__ gz_, const void* __restrict__ hp_, float* __restrict__ gw,
-                 float* __restrict__ gb, int N, int images)
-{
-    constexpr int NOUT = CO * CI * kTaps;
-    constexpr int PER = (NOUT + 255) / 256;
-    __shared__ float gzs[kTileY * kTileX][CO];
-    __shared__ float hps[kHaloY * kHaloX][CI];
+    constexpr int WP = WIDE_IS_GZ ? kTileY * kTileX : kHaloY * kHaloX;   // staged wide pixels
+    constexpr int TP = WIDE_IS_GZ ? kHaloY * kHaloX : kTileY * kTileX;   // staged thin pixels
+    __shared__ __align__(16) float ws[WP][kC];
+    __shared__ float ts[TP];
     const ActGeom G = act_geom(N);
     const int tid = threadIdx.x;
-    float acc[PER];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) acc[k] = 0.0f;
-    float accb = 0.0f;
+    const int cb = tid & 7, tap = (tid >> 3) % kTaps, grp = tid / (8 * kTaps);
+    const int dy = tap / 3, dx = tap % 3;
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f}, accb[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     const int tiles_x = N / kTileX, tiles_y = N / kTileY;
     const long long tiles = (long long)tiles_x * tiles_y * images;
     for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int im = (int)(tile / ((long long)tiles_x * tiles_y));
         const int rem = (int)(tile - (long long)im * tiles_x * tiles_y);
         const int y0 = (rem / tiles_x) * kTileY, x0 = (rem % tiles_x) * kTileX;
-        const size_t img = (size_t)im * N * N;
-        const long long ib = (long long)im * G.plane * kPlanes;
+        const uint4* wi = wide + (long long)im * G.plane * kPlanes;
+        const float* ti = thin + (size_t)im * N * N;
         __syncthreads();                               // previous tile consumed
-        for (int e = tid; e < kTileY * kTileX * CO; e += 256) {
-            const int pix = e / CO, o = e - pix * CO;
-            const int yy = y0 + pix / kTileX, xx = x0 + pix % kTileX;
-            gzs[pix][o] = CO == 1 ? static_cast<const float*>(gz_)[img + (size_t)yy * N + xx]
-                                  : record_channel(static_cast<const uint4*>(gz_) + ib,
-                                                   rec_index(G, yy, xx), o);
+        for (int e = tid; e < WP * kPlanes; e += kWgThinThreads) {
+            const int pix = e / kPlanes, ch = e - pix * kPlanes;
+            const long long r = WIDE_IS_GZ ? rec_index(G, y0 + pix / kTileX, x0 + pix % kTileX)
+                                           : rec_index(G, y0 - 1 + pix / kHaloX, x0 - 1 + pix % kHaloX);
+            float v[8];
+            unpack_record(wi[r * kPlanes + chunk_pos(r, ch)], v);
+            *reinterpret_cast<float4*>(&ws[pix][8 * ch]) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4*>(&ws[pix][8 * ch + 4]) = make_float4(v[4], v[5], v[6], v[7]);
         }
-        for (int e = tid; e < kHaloY * kHaloX * CI; e += 256) {
-            const int pix = e / CI, c = e - pix * CI;
-            const int gy = y0 - 1 + pix / kHaloX, gx = x0 - 1 + pix % kHaloX;
-            float v = 0.0f;
-            if (CI == 1) {
-                if (gy >= 0 && gy < N && gx >= 0 && gx < N)
-                    v = static_cast<const float*>(hp_)[img + (size_t)gy * N + gx];
+        for (int e = tid; e < TP; e += kWgThinThreads) {
+            float v;
+            if (WIDE_IS_GZ) {
+                const int gy = y0 - 1 + e / kHaloX, gx = x0 - 1 + e % kHaloX;
+                v = (gy >= 0 && gy < N && gx >= 0 && gx < N) ? ti[(size_t)gy * N + gx] : 0.0f;
             } else {
-                v = record_channel(static_cast<const uint4*>(hp_) + ib, rec_index(G, gy, gx), c);
+                v = ti[(size_t)(y0 + e / kTileX) * N + x0 + e % kTileX];
             }
-            hps[pix][c] = v;
+            ts[e] = v;
         }
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int e = tid + 256 * k;               // (o, c, tap) in parameter order
-            if (e < NOUT) {
-                const int tap = e % kTaps, c = (e / kTaps) % CI, o = e / (kTaps * CI);
-                const int dy = tap / 3, dx = tap % 3;
-                float s = acc[k];
-                for (int pix = 0; pix < kTileY * kTileX; ++pix) {
-                    const int py = pix / kTileX, px = pix % kTileX;
-                    s = fmaf(gzs[pix][o], hps[(py + dy) * kHaloX + px + dx][c], s);
-                }
-                acc[k] = s;
+#pragma unroll 4
+        for (int p = grp; p < kTileY * kTileX; p += 4) {
+            const int py = p / kTileX, px = p % kTileX;
+            const int ph = (py + dy) * kHaloX + px + dx;               // the tap's halo pixel
+            const float4 w4 = *reinterpret_cast<const float4*>(&ws[WIDE_IS_GZ ? p : ph][4 * cb]);
+            const float t = ts[WIDE_IS_GZ ? ph : p];
+            acc[0] = fmaf(w4.x, t, acc[0]);
+            acc[1] = fmaf(w4.y, t, acc[1]);
+            acc[2] = fmaf(w4.z, t, acc[2]);
+            acc[3] = fmaf(w4.w, t, acc[3]);
+            if (WIDE_IS_GZ && tap == 0) {                              // gb[o] = sum gz
+                accb[0] += w4.x; accb[1] += w4.y; accb[2] += w4.z; accb[3] += w4.w;
             }
+            if (!WIDE_IS_GZ && tap == 0 && cb == 0) accb[0] += t;      // gb[0] = sum gy
         }
-        if (tid < CO)
-            for (int pix = 0; pix < kTileY * kTileX; ++pix) accb += gzs[pix][tid];
     }
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int e = tid + 256 * k;
-        if (e < NOUT) atomicAdd(gw + e, acc[k]);
-    }
-    if (tid < CO) atomicAdd(gb + tid, accb);
+    for (int k = 0; k < 4; ++k) atomicAdd(gw + (size_t)(4 * cb + k) * kTaps + tap, acc[k]);
+    if (WIDE_IS_GZ && tap == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) atomicAdd(gb + 4 * cb + k, accb[k]);
+    if (!WIDE_IS_GZ && tap == 0 && cb == 0) atomicAdd(gb, accb[0]);
 }
 
-// Weight gradient of a 32 -> 32 layer, the same sums as cnn_wgrad_kernel<32, 32> with the
-// work laid out for registers: per 8 x 16-pixel tile the gradient gz (128 pixels) and the
+// Weight gradient of a 32 -> 32 layer: per 8 x 16-pixel tile the gradient gz (128 pixels) and the
 // layer input hp (its 10 x 18-pixel halo) are unpacked to fp32 in shared memory; thread
 // (tap, ob, cb) owns the 4 x 4 block o = 4ob .. 4ob+3, c = 4cb .. 4cb+3 of one tap and
 // sweeps the tile's pixels, two channels per packed FMA.  A warp holds one tap and 4 x 8
@@ -1151,7 +1150,7 @@ cudaError_t backward(const float* params, const float* x, const float* gy, float
     uint4* g[2] = {w.act[5], w.act[6]};
     // layer 6 (32 -> 1): weights from h5 and gy; gradient into z5
     float* gw = gparams + param_offset(5);
-    cnn_wgrad_kernel<1, kC><<<wgrid, 256, 0, st>>>(gy, w.act[4], gw, gw + kC * kTaps, N, batch);
+    cnn_wgrad_thin_kernel<false><<<wgrid, kWgThinThreads, 0, st>>>(w.act[4], gy, gw, gw + kC * kTaps, N, batch);
     cnn_last_backward_kernel<<<rg, 256, 0, st>>>(gy, w.act[4], params + param_offset(5), g[0], N);
     int cur = 0;
     // layers 5 .. 2 (32 -> 32): weights from h_{k-1} and g_z_k; gradient into z_{k-1}
@@ -1166,7 +1165,7 @@ cudaError_t backward(const float* params, const float* x, const float* gy, float
     }
     // layer 1 (1 -> 32): weights from x and g_z1
     gw = gparams;
-    cnn_wgrad_kernel<kC, 1><<<wgrid, 256, 0, st>>>(g[cur], x, gw, gw + kC * kTaps, N, batch);
+    cnn_wgrad_thin_kernel<true><<<wgrid, kWgThinThreads, 0, st>>>(g[cur], x, gw, gw + kC * kTaps, N, batch);
     return cudaGetLastError();
 }
 
