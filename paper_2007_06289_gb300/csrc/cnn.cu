@@ -103,7 +103,12 @@ __host__ __device__ inline ActGeom act_geom(int N)
     g.N = N;
     g.W = N + 2;
     g.T = (int)(((long long)N * g.W + kTileOut - 1) / kTileOut);
-    const long long need = kRecGuard + 2LL * g.W + (long long)kTileOut * g.T + 8;
+    // room for the convolution's runs and for the weight gradient's (256-record tiles,
+    // runs reaching W + 256 records past a tile's start)
+    const long long tw = ((long long)N * g.W + 255) / 256;
+    long long need = kRecGuard + 2LL * g.W + (long long)kTileOut * g.T + 8;
+    const long long need_wg = kRecGuard + 2LL * g.W + 256 * tw + 16;
+    if (need_wg > need) need = need_wg;
     g.plane = (need + 7) & ~7LL;
     return g;
 }
@@ -232,6 +237,14 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t b
     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
                  ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_idesc(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                 ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar)
@@ -679,6 +692,199 @@ cnn_conv32_kernel(ConvArgs a)
     }
 }
 
+// ---------------------------------------------------------------- 32 -> 32 weight gradient on tcgen05
+// gw[o][c][dy][dx] = sum_p gz[p][o] h[p + (dy-1)W + dx - 1][c]
+//                  = sum_q h[q + dx - 1][c] gz[q - (dy-1)W][o]      (q = p + (dy-1)W)
+// over every record q of the padded raster (gz and h are zero off the image).  As one GEMM
+// with the records as K: D[(dx, c)][(dy, o)] = sum_q A[(dx, c)][q] B[(dy, o)][q], both
+// operands "MN-major" in the 64-byte-swizzled layout -- the records themselves, 32 channels
+// contiguous per record, 8 records per 512-byte atom.  A (M = 128) is one run of h whose
+// four 32-row atoms are the same run shifted by one record each (leading-dimension stride 64
+// bytes; atom dx = 3 is a tap that does not exist and is discarded); B (N = 96) is three runs
+// of gz, for dy = 0, 1, 2 records m0 + W, m0, m0 - W on, placed L bytes apart with
+// L / 64 = -W (mod 8) so that every run's rows keep their records' swizzle phase.  A tile is
+// 256 records: 16 MMAs (M = 128, N = 96, K = 16) into one fp32 accumulator that collects all
+// of a CTA's tiles; at the end the epilogue warps read it (lane quarter = dx, lane = c,
+// column = 32 dy + o) and add it into gw.  The bias gradient is cnn_bias_grad_kernel.
+// Roles as in cnn_conv32_kernel: warp 0 copies (one 259-record run of h and three 256-record
+// runs of gz per tile into a 3-stage ring), warp 1 issues the MMAs, warps 2-5 read out.
+constexpr int kWgTile = 256;                              // records (K) per tile
+constexpr int kWgARec = kWgTile + 3;                      // A run: records m0 - 1 .. m0 + 257
+constexpr int kWgABytes = 272 * kRecBytes;                // A buffer: phase + run, in atoms
+constexpr int kWgBBytes = 50 * 1024;                      // B buffer: three runs L apart + phase
+constexpr int kWgStageBytes = kWgABytes + kWgBBytes;
+constexpr int kWgStages = 3;
+constexpr int kWgThreads = 64 + 128;
+constexpr int kWgBarriers = 2 * kWgStages + 2;
+constexpr size_t kWgSmem = 1024 + (size_t)kWgStages * kWgStageBytes + kWgBarriers * 8 + 16;
+constexpr int kWgCols = 128;                              // TMEM columns (96 used)
+constexpr uint32_t kWgIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                              ((uint32_t)(96 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+// MN-major 64-byte-swizzled descriptor: lbo = stride between 32-element atoms along M (or
+// N), sbo = stride between groups of 8 K rows
+__device__ __forceinline__ uint64_t smem_desc_mn64(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (4ull << 61);
+}
+
+__global__ void __launch_bounds__(kWgThreads, 1)
+cnn_wgrad_tc_kernel(const uint4* __restrict__ gz, const uint4* __restrict__ h, float* __restrict__ gw,
+                    int N, int images)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    unsigned char* stages = smem;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stages + (size_t)kWgStages * kWgStageBytes);
+    uint64_t* full = bars;                  // [kWgStages] runs landed
+    uint64_t* empty = bars + kWgStages;     // [kWgStages] runs consumed by the MMAs
+    uint64_t* done = empty + kWgStages;     // every MMA of this CTA complete
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const ActGeom G = act_geom(N);
+    const int T = (int)(((long long)N * G.W + kWgTile - 1) / kWgTile);
+    const long long total = (long long)T * images;
+    // B runs L bytes apart: L / 64 = 256 + (-W mod 8)
+    const uint32_t L = (uint32_t)(256 + ((8 - G.W % 8) & 7)) * kRecBytes;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kWgStages; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_slot)), "n"(kWgCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            long long i = 0;
+            int img = (int)(blockIdx.x / T), tt = (int)(blockIdx.x % T);
+            for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+                const int s = (int)(i % kWgStages);
+                if (i > 0) {
+                    tt += gridDim.x;
+                    while (tt >= T) { tt -= T; ++img; }
+                }
+                if (!wait_bar(empty + s, ((uint32_t)(i / kWgStages) & 1u) ^ 1u, abort_flag)) break;
+                const long long m0 = kRecGuard + G.W + (long long)kWgTile * tt;
+                const long long base = (long long)img * G.plane;
+                unsigned char* st = stages + (size_t)s * kWgStageBytes;
+                mbar_expect_tx(full + s, kWgARec * kRecBytes + 3 * kWgTile * kRecBytes);
+                const long long ra = m0 - 1;                         // A run start
+                bulk_g2s(st + (int)(ra & 7) * kRecBytes, h + (base + ra) * kPlanes, kWgARec * kRecBytes, full + s);
+                unsigned char* bb = st + kWgABytes + (int)((m0 + G.W) & 7) * kRecBytes;
+#pragma unroll 1
+                for (int dy = 0; dy < 3; ++dy) {
+                    const long long rb = m0 - (long long)(dy - 1) * G.W;
+                    bulk_g2s(bb + (size_t)dy * L, gz + (base + rb) * kPlanes, kWgTile * kRecBytes, full + s);
+                }
+            }
+            for (long long j = i - kWgStages; j < i; ++j)
+                if (j >= 0) drain_bar(full + (int)(j % kWgStages), (uint32_t)(j / kWgStages) & 1u);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t sbase = smem_u32(stages);
+            long long i = 0;
+            int tt = (int)(blockIdx.x % T);
+            for (long long t = blockIdx.x; t < total; t += gridDim.x, ++i) {
+                const int s = (int)(i % kWgStages);
+                if (i > 0) {
+                    tt += gridDim.x;
+                    while (tt >= T) tt -= T;
+                }
+                const long long m0 = kRecGuard + G.W + (long long)kWgTile * tt;
+                if (!wait_bar(full + s, (uint32_t)(i / kWgStages) & 1u, abort_flag)) break;
+                tc_fence_after();
+                const uint32_t a0 = sbase + (uint32_t)(s * kWgStageBytes) + (uint32_t)((m0 - 1) & 7) * kRecBytes;
+                const uint32_t b0 = sbase + (uint32_t)(s * kWgStageBytes + kWgABytes) +
+                                    (uint32_t)((m0 + G.W) & 7) * kRecBytes;
+#pragma unroll 4
+                for (int k = 0; k < kWgTile / 16; ++k)
+                    umma_idesc(tmem, smem_desc_mn64(a0 + 1024u * k, kRecBytes, 512),
+                               smem_desc_mn64(b0 + 1024u * k, L, 512), kWgIdesc, (i | k) != 0 ? 1u : 0u);
+                umma_commit(empty + s);
+            }
+            umma_commit(done);
+            drain_bar(done, 0);
+        }
+    } else {
+        // read-out: warp q reads TMEM lane quarter q = dx (q = 3: the discarded tap)
+        const int q = warp & 3;
+        if (q < 3 && blockIdx.x < total && wait_bar(done, 0, abort_flag)) {
+            tc_fence_after();
+            for (int c0 = 0; c0 < 96; c0 += 32) {
+                uint32_t v[32];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                             "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                             "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                               "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                               "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
+                               "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                               "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+                               "=r"(v[30]), "=r"(v[31])
+                             : "r"(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0));
+                tmem_wait_ld();
+                const int dy = c0 / 32, c = lane;
+#pragma unroll
+                for (int o = 0; o < 32; ++o)
+                    atomicAdd(gw + ((size_t)(o * kC + c) * 3 + dy) * 3 + q, __uint_as_float(v[o]));
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kWgCols) : "memory");
+    }
+}
+
+// gb[o] += sum over every record of gz of channel o (zero off the image): one record per
+// thread and step, 32 fp32 sums per thread, reduced across the CTA in shared memory.
+__global__ void __launch_bounds__(256)
+cnn_bias_grad_kernel(const uint4* __restrict__ gz, float* __restrict__ gb, long long records)
+{
+    __shared__ float red[kC];
+    float acc[kC];
+#pragma unroll
+    for (int c = 0; c < kC; ++c) acc[c] = 0.0f;
+    if (threadIdx.x < kC) red[threadIdx.x] = 0.0f;
+    __syncthreads();
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < records;
+         r += (long long)gridDim.x * blockDim.x) {
+        float v[kC];
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) unpack_record(gz[r * kPlanes + chunk_pos(r, p)], v + 8 * p);
+#pragma unroll
+        for (int c = 0; c < kC; ++c) acc[c] += v[c];
+    }
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+        float x = acc[c];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&red[c], x);
+    }
+    __syncthreads();
+    if (threadIdx.x < kC) atomicAdd(gb + threadIdx.x, red[threadIdx.x]);
+}
+
 // ---------------------------------------------------------------- 1 -> 32 and 32 -> 1
 // First layer: h[p][o] = relu(b[o] + sum_tap w[o][tap] x[p + off(tap)]), fp32 math, written
 // as records over the whole plane (zero outside the image).  CTA (row segment, row y,
@@ -939,82 +1145,6 @@ cnn_wgrad_thin_kernel(const uint4* __restrict__ wide, const float* __restrict__ 
     if (!WIDE_IS_GZ && tap == 0 && cb == 0) atomicAdd(gb, accb[0]);
 }
 
-// Weight gradient of a 32 -> 32 layer: per 8 x 16-pixel tile the gradient gz (128 pixels) and the
-// layer input hp (its 10 x 18-pixel halo) are unpacked to fp32 in shared memory; thread
-// (tap, ob, cb) owns the 4 x 4 block o = 4ob .. 4ob+3, c = 4cb .. 4cb+3 of one tap and
-// sweeps the tile's pixels, two channels per packed FMA.  A warp holds one tap and 4 x 8
-// blocks, so its 16-byte shared loads read 4 (gz) and 8 (hp) distinct addresses.  Threads
-// 0..31 sum the bias gradient of their channel.  Persistent CTAs add into gw and gb once.
-constexpr int kWg32Threads = kTaps * 64;
-__global__ void __launch_bounds__(kWg32Threads, 2)
-cnn_wgrad32_kernel(const uint4* __restrict__ gz, const uint4* __restrict__ hp, float* __restrict__ gw,
-                   float* __restrict__ gb, int N, int images)
-{
-    __shared__ __align__(16) float gzs[kTileY * kTileX][kC];
-    __shared__ __align__(16) float hps[kHaloY * kHaloX][kC];
-    const ActGeom G = act_geom(N);
-    const int tid = threadIdx.x;
-    const int tap = tid >> 6, ob = (tid >> 3) & 7, cb = tid & 7;
-    const int dy = tap / 3, dx = tap % 3;
-    float2 acc[4][2];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k][0] = acc[k][1] = make_float2(0.0f, 0.0f);
-    float accb = 0.0f;
-    const int tiles_x = N / kTileX, tiles_y = N / kTileY;
-    const long long tiles = (long long)tiles_x * tiles_y * images;
-    for (long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int im = (int)(tile / ((long long)tiles_x * tiles_y));
-        const int rem = (int)(tile - (long long)im * tiles_x * tiles_y);
-        const int y0 = (rem / tiles_x) * kTileY, x0 = (rem % tiles_x) * kTileX;
-        const uint4* gzi = gz + (long long)im * G.plane * kPlanes;
-        const uint4* hpi = hp + (long long)im * G.plane * kPlanes;
-        __syncthreads();                               // previous tile consumed
-        for (int e = tid; e < kTileY * kTileX * kPlanes; e += kWg32Threads) {
-            const int pix = e / kPlanes, ch = e - pix * kPlanes;
-            const long long r = rec_index(G, y0 + pix / kTileX, x0 + pix % kTileX);
-            float v[8];
-            unpack_record(gzi[r * kPlanes + chunk_pos(r, ch)], v);
-            *reinterpret_cast<float4*>(&gzs[pix][8 * ch]) = make_float4(v[0], v[1], v[2], v[3]);
-            *reinterpret_cast<float4*>(&gzs[pix][8 * ch + 4]) = make_float4(v[4], v[5], v[6], v[7]);
-        }
-        for (int e = tid; e < kHaloY * kHaloX * kPlanes; e += kWg32Threads) {
-            const int pix = e / kPlanes, ch = e - pix * kPlanes;
-            const long long r = rec_index(G, y0 - 1 + pix / kHaloX, x0 - 1 + pix % kHaloX);
-            float v[8];
-            unpack_record(hpi[r * kPlanes + chunk_pos(r, ch)], v);
-            *reinterpret_cast<float4*>(&hps[pix][8 * ch]) = make_float4(v[0], v[1], v[2], v[3]);
-            *reinterpret_cast<float4*>(&hps[pix][8 * ch + 4]) = make_float4(v[4], v[5], v[6], v[7]);
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int p = 0; p < kTileY * kTileX; ++p) {
-            const int py = p / kTileX, px = p % kTileX;
-            const float4 g4 = *reinterpret_cast<const float4*>(&gzs[p][4 * ob]);
-            const float4 h4 = *reinterpret_cast<const float4*>(&hps[(py + dy) * kHaloX + px + dx][4 * cb]);
-            const float2 h01 = make_float2(h4.x, h4.y), h23 = make_float2(h4.z, h4.w);
-            const float gk[4] = {g4.x, g4.y, g4.z, g4.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float2 g2 = make_float2(gk[k], gk[k]);
-                acc[k][0] = __ffma2_rn(g2, h01, acc[k][0]);
-                acc[k][1] = __ffma2_rn(g2, h23, acc[k][1]);
-            }
-        }
-        if (tid < kC)
-            for (int p = 0; p < kTileY * kTileX; ++p) accb += gzs[p][tid];
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int o = 4 * ob + k;
-        float* dst = gw + ((size_t)o * kC + 4 * cb) * kTaps + tap;
-        atomicAdd(dst, acc[k][0].x);
-        atomicAdd(dst + kTaps, acc[k][0].y);
-        atomicAdd(dst + 2 * kTaps, acc[k][1].x);
-        atomicAdd(dst + 3 * kTaps, acc[k][1].y);
-    }
-    if (tid < kC) atomicAdd(gb + tid, accb);
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------- host side
@@ -1104,6 +1234,34 @@ cudaError_t launch_conv32(const uint4* in, const bf16* wt, const float* bias, co
     return cudaGetLastError();
 }
 
+cudaError_t launch_wgrad_tc(const uint4* gz, const uint4* h, float* gw, float* gb, int N, int batch,
+                            int sms, cudaStream_t st)
+{
+    static std::mutex lock;
+    static bool done[kMaxCnnDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxCnnDevices) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> g(lock);
+        if (!done[dev]) {
+            e = cudaFuncSetAttribute(cnn_wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kWgSmem);
+            if (e != cudaSuccess) return e;
+            done[dev] = true;
+        }
+    }
+    const ActGeom G = act_geom(N);
+    const long long tiles = ((long long)N * G.W + kWgTile - 1) / kWgTile * batch;
+    const int grid = (int)(tiles < sms ? tiles : sms);
+    cnn_wgrad_tc_kernel<<<grid, kWgThreads, kWgSmem, st>>>(gz, h, gw, N, batch);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cnn_bias_grad_kernel<<<2 * sms, 256, 0, st>>>(gz, gb, (long long)batch * G.plane);
+    return cudaGetLastError();
+}
+
 int device_sms()
 {
     int dev = 0, sms = 0;
@@ -1156,8 +1314,8 @@ cudaError_t backward(const float* params, const float* x, const float* gy, float
     // layers 5 .. 2 (32 -> 32): weights from h_{k-1} and g_z_k; gradient into z_{k-1}
     for (int k = 4; k >= 1; --k) {
         gw = gparams + param_offset(k);
-        cnn_wgrad32_kernel<<<wgrid, kWg32Threads, 0, st>>>(g[cur], w.act[k - 1], gw,
-                                                           gw + kC * kC * kTaps, N, batch);
+        e = launch_wgrad_tc(g[cur], w.act[k - 1], gw, gw + kC * kC * kTaps, N, batch, sms, st);
+        if (e != cudaSuccess) return e;
         e = launch_conv32<false, false, true>(g[cur], w.wb[k - 1], nullptr, w.act[k - 1],
                                               g[cur ^ 1], N, batch, sms, st);
         if (e != cudaSuccess) return e;
