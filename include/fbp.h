@@ -220,8 +220,9 @@ fbp_status fbp_sirt(fbp_plan_t plan, const float* d_lin_data, float* d_img, int 
  * 32 -> 32 layers run as bf16 implicit GEMMs on the tcgen05 tensor cores (accumulators in
  * tensor memory, fp32; operands staged by bulk copies), hidden activations and gradients
  * stored as bf16.  The 32 -> 1 layer runs on the tensor cores too, its fp32 weights split
- * exactly into three bf16 parts; the first layer and the weight gradients run in fp32 on
- * the CUDA cores.  Images:
+ * exactly into three bf16 parts, and so do the hidden layers' weight gradients (fp32
+ * accumulation over all pixels); the first layer and the 1-channel layers' weight
+ * gradients run in fp32 on the CUDA cores.  Images:
  * [batch][N][N] fp32, N a power of two in 16..4096.  The caller provides the workspace
  * (16-byte aligned).  Calls that share a workspace must not overlap on the GPU. */
 size_t fbp_cnn_param_count(void);

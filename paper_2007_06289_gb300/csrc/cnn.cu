@@ -44,8 +44,10 @@
 //
 // The 32 -> 1 layer runs in the same tensor-core kernel (its fp32 weights split exactly
 // into three bf16 parts, so that the products and their fp32 sums are those of the fp32
-// weights).  The 1 -> 32 layer, the last layer's gradient and the weight gradients run on
-// the CUDA cores in fp32.  The data gradient of a 32 -> 32 layer is the same tensor-core
+// weights).  The weight gradients of the 32 -> 32 layers are a tensor-core GEMM over the
+// records (cnn_wgrad_tc_kernel).  The 1 -> 32 layer, the last layer's gradient and the
+// 1-channel layers' weight gradients run on the CUDA cores in fp32.  The data gradient of a
+// 32 -> 32 layer is the same tensor-core
 // kernel with the layer's weights transposed (input and output channels swapped, taps
 // mirrored) and the previous layer's ReLU applied as a mask.
 //
