@@ -1260,7 +1260,7 @@ cudaError_t launch_wgrad_tc(const uint4* gz, const uint4* h, float* gw, float* g
     cnn_wgrad_tc_kernel<<<grid, kWgThreads, kWgSmem, st>>>(gz, h, gw, N, batch);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    cnn_bias_grad_kernel<<<2 * sms, 256, 0, st>>>(gz, gb, (long long)batch * G.plane);
+    cnn_bias_grad_kernel<<<8 * sms, 256, 0, st>>>(gz, gb, (long long)batch * G.plane);
     return cudaGetLastError();
 }
 
@@ -1306,7 +1306,7 @@ cudaError_t backward(const float* params, const float* x, const float* gy, float
     if (e != cudaSuccess) return e;
     const ActGeom G = act_geom(N);
     const dim3 rg((unsigned)((G.plane + 255) / 256), batch);
-    const int wgrid = 2 * sms;
+    const int wgrid = 8 * sms;             // persistent reductions: enough CTAs to hide their loads
     uint4* g[2] = {w.act[5], w.act[6]};
     // layer 6 (32 -> 1): weights from h5 and gy; gradient into z5
     float* gw = gparams + param_offset(5);
