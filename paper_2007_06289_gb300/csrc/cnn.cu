@@ -1280,7 +1280,7 @@ cudaError_t forward(const float* params, const float* x, float* y, void* ws, int
     for (int k = 0; k < 4; ++k)
         cnn_prep_weights_kernel<<<(kWChunks * kWRows * 8 + 255) / 256, 256, 0, st>>>(
             params + param_offset(k + 1), w.wf[k], w.wb[k]);
-    const ActGeom G = act_geom(N);
+    // the first layer: row segments x (N image rows + one row of pad / guard / tail zeroing)
     const dim3 fg((unsigned)((N + kFirstPx * kFirstThreads - 1) / (kFirstPx * kFirstThreads)), N + 1, batch);
     // h1 .. h5 in act[0..4] when saving for the backward pass, else ping-pong in act[0..1]
     auto hbuf = [&](int k) { return save ? w.act[k] : w.act[k & 1]; };
