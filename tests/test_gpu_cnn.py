@@ -185,6 +185,66 @@ def test_gradients_match_oracle_elementwise(fbp, torch):
         off += n
 
 
+def window_forward(ps, x, y0, x0, storage):
+    """The network's output at pixel (y0, x0) of the N x N image x, from the 13 x 13 window
+    of inputs around it (six 3 x 3 layers: an output depends on inputs within 6 pixels).  The
+    oracle's layers run on the window, each layer's values zeroed off the image as the
+    network's zero padding does; the window's own edge only corrupts values that no longer
+    reach the centre."""
+    N, R = x.shape[-1], 6
+    ys, xs = np.arange(y0 - R, y0 + R + 1), np.arange(x0 - R, x0 + R + 1)
+    inside = ((ys[:, None] >= 0) & (ys[:, None] < N) & (xs[None, :] >= 0) & (xs[None, :] < N))
+    win = np.where(inside, x[np.clip(ys, 0, N - 1)][:, np.clip(xs, 0, N - 1)], 0.0)
+    stored = ocnn._stored(ps, storage)
+    h = win[None]
+    for k, (w, b) in enumerate(stored):
+        z = ocnn.conv3x3(h, w, b)
+        if k < len(stored) - 1:
+            h = np.maximum(z, 0.0)
+            if storage == "bf16":
+                h = ocnn.bf16(h)
+            h = h * inside
+        else:
+            h = z
+    return win[R, R] + h[0, R, R]
+
+
+def sample_pixels(rng, N, n):
+    """Corners, the middle of every edge and random pixels (row ends straddle tiles)."""
+    fixed = [(0, 0), (0, N - 1), (N - 1, 0), (N - 1, N - 1), (0, N // 2), (N - 1, N // 2),
+             (N // 2, 0), (N // 2, N - 1), (1, 1), (N - 2, N - 2)]
+    rand = [tuple(p) for p in rng.integers(0, N, size=(n - len(fixed), 2))]
+    return fixed + rand
+
+
+def test_full_size_sampled_pixels_match_oracle(fbp, torch):
+    """N = 2048 (the inference size of the benchmark), two images: an integer network bit for
+    bit and a random network within the first-order bfloat16 bound, at sampled pixels
+    (corners, edges, interior) evaluated one by one by the oracle on their input windows."""
+    N, B = 2048, 2
+    rng = np.random.default_rng(2048)
+    pix = sample_pixels(rng, N, 40)
+    # integer network: exact
+    ps = int_params(9)
+    x = int_images(rng, (B, N, N), 0.6)
+    y, _ = run_gpu(fbp, torch, flatten(ps), x)
+    for b in range(B):
+        for (py, px) in pix:
+            want = window_forward(ps, x[b], py, px, "bf16")
+            assert y[b, py, px] == want, (b, py, px, y[b, py, px], want)
+    # random network: within 5 * 2^-7 * A of the bfloat16-storage oracle
+    flat = random_params(3, rng)
+    x = smooth_images(rng, B, N).astype(np.float32).astype(np.float64)
+    y, _ = run_gpu(fbp, torch, flat, x)
+    ps = unflatten(flat)
+    aps = [(np.abs(w), np.abs(bb)) for w, bb in ps]
+    for b in range(B):
+        for (py, px) in pix:
+            want = window_forward(ps, x[b], py, px, "bf16")
+            A = window_forward(aps, np.abs(x[b]), py, px, "f64") - abs(x[b, py, px])
+            assert abs(y[b, py, px] - want) <= 5 * U7 * A + 1e-6 * abs(want), (b, py, px)
+
+
 def test_training_reduces_the_error_to_direct_fbp(fbp, torch):
     from paper_2007_06289_gb300 import corrector
     N, S = 64, 16
