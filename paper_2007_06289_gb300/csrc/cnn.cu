@@ -75,7 +75,9 @@ constexpr int kStageBytes = 3 * kRunBytes;                 // 50688
 constexpr int kStages = 3;
 constexpr int kWRows = 128;                                // A rows: (lane quarter, dx, channel)
 constexpr int kWChunks = 3 * kPlanes;                      // 12 K chunks of 8: (dy, input channel / 8)
-constexpr int kWBytes = kWChunks * kWRows * 16;            // 24576
+constexpr int kWImgChunks = kWChunks + 2;                  // + one K step: the bias in three bf16 parts
+constexpr int kWBytes = kWImgChunks * kWRows * 16;         // 28672
+constexpr int kOnesBytes = 2 * kNpix * 16;                 // the bias step's B operand: all ones
 constexpr int kAcc = 2;           // TMEM accumulators (256 columns each)
 constexpr int kTmemCols = 512;
 constexpr int kEpiGroups = 4;     // epilogue warpgroups, all sharing every tile
@@ -84,7 +86,7 @@ static_assert(kChunksPerEpi == 2, "each epilogue warp reads two chunks with one 
 constexpr int kConvThreads = 64 + 128 * kEpiGroups;
 constexpr int kBarriers = 2 * kStages + 2 * kAcc + 2;
 constexpr int kScratchBytes = 4 * kEpiGroups * 512;        // per epilogue warp: 32 pixels x 8 channels bf16
-constexpr size_t kConvSmem = 1024 + (size_t)kWBytes + (size_t)kStages * kStageBytes + kScratchBytes +
+constexpr size_t kConvSmem = 1024 + (size_t)kWBytes + kOnesBytes + (size_t)kStages * kStageBytes + kScratchBytes +
                              kBarriers * 8 + 16;
 constexpr int kTileY = 8, kTileX = 16;           // pixels per tile of the weight-gradient kernel
 constexpr int kHaloY = kTileY + 2, kHaloX = kTileX + 2;
@@ -318,19 +320,41 @@ __device__ __forceinline__ void unpack_record(const uint4 r, float* v)
 }
 
 // ---------------------------------------------------------------- weight preparation
+// A float32 value as the exact sum of three bf16 values, hi = bf16(v), mid = bf16(v - hi),
+// lo = bf16(v - hi - mid): after two bf16 parts at most 8 significant bits are left.
+__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// part 0, 1, 2 (hi, mid, lo) of v split exactly into three bf16 values
+__device__ __forceinline__ float bf16_part(float v, int part)
+{
+    const float hi = bf16_round(v);
+    const float mid = bf16_round(v - hi);
+    const float lo = bf16_round((v - hi) - mid);
+    return part == 0 ? hi : (part == 1 ? mid : lo);
+}
+
 // fp32 [co][ci][3][3] of a 32 -> 32 layer -> the shared-memory image of the GEMM's A operand:
 // K chunk (dy * 4 + input channel / 8), then row 32 (o / 8) + 8 dx + o % 8, then input
 // channel % 8 (rows 32 q + 24 .. 32 q + 31 zero).  Forward: output o = co, input ci, tap
 // (dy, dx).  Data gradient (transposed convolution): output o = ci, input co, tap
-// (2 - dy, 2 - dx).  One thread per element of the image.
+// (2 - dy, 2 - dx).  Chunks 12 and 13 are the bias step of the forward image: K column p of
+// row 32q + o' (tap dx = 0) holds part p (bf16_part) of output channel 8q + o''s bias,
+// multiplied by a B operand of ones; everything else there is zero.  One thread per element of the image.
 __global__ void cnn_prep_weights_kernel(const float* __restrict__ w, bf16* __restrict__ fwd,
                                         bf16* __restrict__ bwd)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;      // (chunk, row, lane of 8)
-    if (e >= kWChunks * kWRows * 8) return;
+    if (e >= kWImgChunks * kWRows * 8) return;
     const int c8 = e & 7;
     const int row = (e >> 3) % kWRows;
     const int chunk = e / (8 * kWRows);
+    if (chunk >= kWChunks) {
+        const int q = row / 32, dx = (row % 32) / 8, ol = row % 8;
+        const bool part = chunk == kWChunks && dx == 0 && c8 < 3;
+        fwd[e] = __float2bfloat16_rn(part ? bf16_part(w[kC * kC * kTaps + 8 * q + ol], c8) : 0.0f);
+        bwd[e] = __float2bfloat16_rn(0.0f);
+        return;
+    }
     const int dy = chunk / kPlanes, cin = (chunk % kPlanes) * 8 + c8;
     const int q = row / 32, dx = (row % 32) / 8, ol = row % 8;
     const int o = 8 * q + ol;
@@ -348,26 +372,23 @@ __global__ void cnn_prep_weights_kernel(const float* __restrict__ w, bf16* __res
 // hi - mid): two bf16 parts leave at most 8 significant bits, which the third holds), as
 // "output channels" 0, 1, 2 (rows 32q + 8 dx + part) of every lane quarter q, so that all
 // epilogue warps can read them; the other rows zero.
-__device__ __forceinline__ float bf16_round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 __global__ void cnn_prep_last_kernel(const float* __restrict__ w, bf16* __restrict__ img)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;      // (chunk, row, lane of 8)
-    if (e >= kWChunks * kWRows * 8) return;
+    if (e >= kWImgChunks * kWRows * 8) return;
     const int c8 = e & 7;
     const int row = (e >> 3) % kWRows;
     const int chunk = e / (8 * kWRows);
+    if (chunk >= kWChunks) {                                  // no bias step: its bias is added later
+        img[e] = __float2bfloat16_rn(0.0f);
+        return;
+    }
     const int dy = chunk / kPlanes, cin = (chunk % kPlanes) * 8 + c8;
     const int q = row / 32, dx = (row % 32) / 8, part = row % 8;
     float v = 0.0f;
     (void)q;
-    if (dx < 3 && part < 3) {
-        const float wv = w[(cin * 3 + dy) * 3 + dx];
-        const float hi = bf16_round(wv);
-        const float mid = bf16_round(wv - hi);
-        const float lo = bf16_round((wv - hi) - mid);
-        v = part == 0 ? hi : (part == 1 ? mid : lo);
-    }
+    if (dx < 3 && part < 3) v = bf16_part(w[(cin * 3 + dy) * 3 + dx], part);
     img[e] = __float2bfloat16_rn(v);
 }
 
@@ -395,7 +416,8 @@ cnn_conv32_kernel(ConvArgs a)
     // run buffers must start on 512-byte atoms: align the carve to 1 KB
     unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char* wsm = smem;
-    unsigned char* stages = smem + kWBytes;
+    unsigned char* ones = smem + kWBytes;                                // bias step's B: bf16 ones
+    unsigned char* stages = ones + kOnesBytes;
     unsigned char* scratch = stages + (size_t)kStages * kStageBytes;     // 512 bytes per epilogue warp
     uint64_t* bars = reinterpret_cast<uint64_t*>(scratch + kScratchBytes);
     uint64_t* full = bars;                  // [kStages] runs landed
@@ -429,6 +451,11 @@ cnn_conv32_kernel(ConvArgs a)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      ::"r"(smem_u32(tmem_slot)), "n"(kTmemCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (BIAS) {
+        for (int i = threadIdx.x; i < kOnesBytes / 16; i += blockDim.x)
+            reinterpret_cast<uint4*>(ones)[i] = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor cores
     }
     tc_fence_before();
     __syncthreads();
@@ -500,6 +527,9 @@ cnn_conv32_kernel(ConvArgs a)
                             umma(d, ad, bd, (dy | kk) != 0 ? 1u : 0u);
                         }
                     }
+                    if (BIAS)                          // + bias (three parts) x ones, every column
+                        umma(d, smem_desc(wbase + (uint32_t)(kWChunks * kWRows * 16), kWRows * 16, 128),
+                             smem_desc(smem_u32(ones), kNpix * 16, 128), 1u);
                     umma_commit(empty + s);
                     umma_commit(tfull + b);
                 }
@@ -533,10 +563,10 @@ cnn_conv32_kernel(ConvArgs a)
         // 32q + 15) and of tap 2 (load Q, lanes 32q + 16 ..).  Output pixel k needs tap dx at
         // column k + dx: for the pair (2m, 2m + 1) the columns 2m + 2, 2m + 3 come from the
         // neighbour m + 1, or for m = 3 from lane m = 0's next group.
-        const int g = lane >> 2, m = lane & 3;
+        const int m = lane & 3;
         const int nb = (lane & ~3) | ((lane + 1) & 3);
         const int c0 = eg * kChunksPerEpi;               // this group's first 32-column chunk
-        const float bias = BIAS ? __ldg(a.bias + 8 * q + g) : (LAST ? __ldg(a.bias) : 0.0f);
+        const float bias = LAST ? __ldg(a.bias) : 0.0f;   // the hidden layers' biases come from the MMAs
         unsigned char* scr = scratch + (size_t)(warp - 2) * 512;    // [32 px][8 ch] bf16
         long long i = 0;
         int img = (int)(blockIdx.x / G.T), tt = (int)(blockIdx.x % G.T);
@@ -649,7 +679,6 @@ cnn_conv32_kernel(ConvArgs a)
                     const float xb = __shfl_sync(0xffffffffu, sb, nb);
                     float o0 = (__uint_as_float(P[4 * r]) + __uint_as_float(P[4 * r + 3])) + xa;
                     float o1 = __uint_as_float(P[4 * r + 1]) + xb;
-                    if (BIAS) { o0 += bias; o1 += bias; }
                     __nv_bfloat162 pk = __floats2bfloat162_rn(o0, o1);
                     // ReLU after rounding: rounding is monotone and keeps 0, so this equals
                     // rounding the rectified value
@@ -1278,7 +1307,7 @@ cudaError_t forward(const float* params, const float* x, float* y, void* ws, int
 {
     Ws w = carve(ws, N, batch, save);
     for (int k = 0; k < 4; ++k)
-        cnn_prep_weights_kernel<<<(kWChunks * kWRows * 8 + 255) / 256, 256, 0, st>>>(
+        cnn_prep_weights_kernel<<<(kWImgChunks * kWRows * 8 + 255) / 256, 256, 0, st>>>(
             params + param_offset(k + 1), w.wf[k], w.wb[k]);
     // the first layer: row segments x (N image rows + one row of pad / guard / tail zeroing)
     const dim3 fg((unsigned)((N + kFirstPx * kFirstThreads - 1) / (kFirstPx * kFirstThreads)), N + 1, batch);
@@ -1293,7 +1322,7 @@ cudaError_t forward(const float* params, const float* x, float* y, void* ws, int
                                                                nullptr, hbuf(k), N, batch, sms, st);
         if (e != cudaSuccess) return e;
     }
-    cnn_prep_last_kernel<<<(kWChunks * kWRows * 8 + 255) / 256, 256, 0, st>>>(params + param_offset(5), w.wl);
+    cnn_prep_last_kernel<<<(kWImgChunks * kWRows * 8 + 255) / 256, 256, 0, st>>>(params + param_offset(5), w.wl);
     return launch_conv32<false, false, false, true>(hbuf(4), w.wl, params + param_offset(5) + kC * kTaps,
                                                     nullptr, nullptr, N, batch, sms, st, x, y);
 }
