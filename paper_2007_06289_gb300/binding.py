@@ -100,6 +100,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     }
     if hasattr(lib, "fbp_check_set_row_angle"):           # bounds-checked build only
         sig["fbp_check_set_row_angle"] = (I, [P, I, I, I])
+        sig["fbp_check_cnn_image_limit"] = (I, [I])
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
         fn.restype = res
@@ -511,3 +512,8 @@ def fbp_check_set_row_angle(plan: Plan, q: int, i: int, k0: int) -> None:
     """Test hook of the bounds-checked library (include/fbp_check.h)."""
     _check("fbp_check_set_row_angle",
            load_library().fbp_check_set_row_angle(plan.handle, int(q), int(i), int(k0)))
+
+
+def fbp_check_cnn_image_limit(images: int) -> None:
+    """Test hook of the bounds-checked library (include/fbp_check.h)."""
+    _check("fbp_check_cnn_image_limit", load_library().fbp_check_cnn_image_limit(int(images)))

@@ -54,11 +54,14 @@ constexpr int kAfPitch = kAfCols + 1;           // odd: conflict-free column-wis
 template <int S> constexpr size_t af_smem() { return 2 * (size_t)(1 << S) * kAfPitch * sizeof(float); }
 
 // RESID (last launch only): the output is turned into the SIRT residual on the way out,
-// (b - out) * rinv, b [count][4][N][2N] and rinv one slice's [4][N][2N].
+// (b - out) * rinv, b [count][4][N][2N] and rinv one slice's [4][N][2N].  `in` holds in_n
+// floats and `out` out_n (b: out_n, rinv: out_n / count); in the bounds-checked build every
+// global index is tested against them.
 template <int S, bool FROM_IMAGE, bool RESID>
 __global__ void __launch_bounds__(kAdjThreads)
 adj_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int N, int n, int k,
-                 int wc, const float* __restrict__ rb, const float* __restrict__ rw)
+                 int wc, const float* __restrict__ rb, const float* __restrict__ rw,
+                 long long in_n, long long out_n, long long rw_n, int* status)
 {
     constexpr int R = 1 << S;
     constexpr int H = af_halo<S>();
@@ -74,6 +77,7 @@ adj_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int N, i
     const int x0 = xa + blockIdx.x * T;         // first output column (before the C t skew)
     if (x0 >= W) return;                        // every output column x + C t >= W
     const int xs = x0 - H;                      // column of shared column 0
+    const Span si{in, in_n, status};
 
     // load the group's rows: shared row j, column p <-> input column xs + p
     float* X = sm;
@@ -89,7 +93,7 @@ adj_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int N, i
             const int u = q == 0 ? x : N - 1 - x;
             float v[R];                         // all of the rows' loads in flight at once
 #pragma unroll
-            for (int j = 0; j < R; ++j) v[j] = ok ? gi[(size_t)(tau0 + j) * N + u] : 0.0f;
+            for (int j = 0; j < R; ++j) v[j] = ok ? ld_in(si, gi + (size_t)(tau0 + j) * N + u) : 0.0f;
 #pragma unroll
             for (int j = 0; j < R; ++j) X[j * kAfPitch + tid] = v[j];
         } else {
@@ -102,7 +106,7 @@ adj_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int N, i
                 const int x = xs + (idx >> S);
                 const bool ok = x >= 0 && x < N;
                 const int u = q == 2 ? x : N - 1 - x;
-                v[it] = ok ? gi[(size_t)u * N + tau0 + j] : 0.0f;
+                v[it] = ok ? ld_in(si, gi + (size_t)u * N + tau0 + j) : 0.0f;
             }
 #pragma unroll
             for (int it = 0; it < R; ++it) {
@@ -119,7 +123,7 @@ adj_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int N, i
         for (int j = 0; j < R; ++j) {
             const int lo = xa + b * j;          // b (2^S t + j)
             const int hi = min(W, lo + span);
-            v[j] = (x >= lo && x < hi) ? rows[(size_t)j * W + x] : 0.0f;
+            v[j] = (x >= lo && x < hi) ? ld_in(si, rows + (size_t)j * W + x) : 0.0f;
         }
 #pragma unroll
         for (int j = 0; j < R; ++j) X[j * kAfPitch + tid] = v[j];
@@ -132,10 +136,11 @@ adj_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int N, i
         const bool ok = tid >= H && x < xa + wc && x < W;
         const size_t o = ((size_t)sq * N + ((size_t)b << S)) * W + x;
         const size_t ow = o - (size_t)(sq >> 2) * 4 * N * W;
+        const Span sb{rb, out_n, status}, sw{rw, rw_n, status};
 #pragma unroll
         for (int C = 0; C < R; ++C) {
-            rbv[C] = ok ? rb[o + (size_t)C * W] : 0.0f;
-            rwv[C] = ok ? rw[ow + (size_t)C * W] : 0.0f;
+            rbv[C] = ok ? ld_in(sb, rb + o + (size_t)C * W) : 0.0f;
+            rwv[C] = ok ? ld_in(sw, rw + ow + (size_t)C * W) : 0.0f;
         }
     }
     __syncthreads();
@@ -174,6 +179,7 @@ adj_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int N, i
     // for x below the end of the written range xa + wc
     if (p >= H) {
         const int x = xs + p;
+        const Span so{out, out_n, status};
         if (x < xa + wc) {
             const size_t o = ((size_t)sq * N + ((size_t)b << (S + ko)) + t) * W + x;
 #pragma unroll
@@ -183,7 +189,7 @@ adj_fused_kernel(const float* __restrict__ in, float* __restrict__ out, int N, i
                     const size_t oc = o + ((size_t)C << ko) * W + (size_t)C * t;
                     float val = cur[C * kAfPitch + p];
                     if constexpr (RESID) val = (rbv[C] - val) * rwv[C];
-                    out[oc] = val;
+                    if (so.ok(out + oc)) out[oc] = val;
                 }
             }
         }
@@ -204,22 +210,29 @@ cudaError_t set_af_attr()
 
 template <int S>
 cudaError_t launch_af(const float* in, float* out, int N, int n, int k, int count, bool from_image,
-                      const float* rb, const float* rw, cudaStream_t st)
+                      const float* rb, const float* rw, int* status, cudaStream_t st)
 {
     const int W = 2 * N;
+    const long long lin_n = (long long)count * 4 * N * W;
+    const long long in_n = from_image ? (long long)count * N * N : lin_n;
+    const long long rw_n = (long long)4 * N * W;
     // written length of every output row: the last launch (level 0) writes all W columns
     const int wc = k == S ? W : N + (1 << (n - k + S)) - 1;
     const dim3 grid((wc + af_tile<S>() - 1) / af_tile<S>(), N >> S, 4 * count);
     const size_t sm = af_smem<S>();
     const bool resid = rb != nullptr && k == S;
     if (from_image && resid)
-        adj_fused_kernel<S, true, true><<<grid, kAdjThreads, sm, st>>>(in, out, N, n, k, wc, rb, rw);
+        adj_fused_kernel<S, true, true><<<grid, kAdjThreads, sm, st>>>(in, out, N, n, k, wc, rb, rw,
+                                                                          in_n, lin_n, rw_n, status);
     else if (from_image)
-        adj_fused_kernel<S, true, false><<<grid, kAdjThreads, sm, st>>>(in, out, N, n, k, wc, rb, rw);
+        adj_fused_kernel<S, true, false><<<grid, kAdjThreads, sm, st>>>(in, out, N, n, k, wc, rb, rw,
+                                                                          in_n, lin_n, rw_n, status);
     else if (resid)
-        adj_fused_kernel<S, false, true><<<grid, kAdjThreads, sm, st>>>(in, out, N, n, k, wc, rb, rw);
+        adj_fused_kernel<S, false, true><<<grid, kAdjThreads, sm, st>>>(in, out, N, n, k, wc, rb, rw,
+                                                                          in_n, lin_n, rw_n, status);
     else
-        adj_fused_kernel<S, false, false><<<grid, kAdjThreads, sm, st>>>(in, out, N, n, k, wc, rb, rw);
+        adj_fused_kernel<S, false, false><<<grid, kAdjThreads, sm, st>>>(in, out, N, n, k, wc, rb, rw,
+                                                                          in_n, lin_n, rw_n, status);
     return cudaGetLastError();
 }
 
@@ -239,10 +252,13 @@ constexpr int kRsEnt = 32;                      // reader rows staged per round
 constexpr int kRsBins = 4;                      // bins per thread (s0 .. s3)
 constexpr int kRsWin = 10;                      // columns a thread reads per reader row
 
+// count slices; in the bounds-checked build every global index (the tables' included) is
+// tested against its buffer.
 __global__ void __launch_bounds__(kAdjThreads, 1)
 adj_resample_kernel(const float* __restrict__ lbar, float* __restrict__ pbar,
                     const RowGeom* __restrict__ geom, const int* __restrict__ rptr,
-                    const ReaderEntry* __restrict__ rent, int N, int K, int M)
+                    const ReaderEntry* __restrict__ rent, int N, int K, int M, int count,
+                    int n_ent, int* status)
 {
     __shared__ long long ea[kRsEnt], eb[kRsEnt];    // m(c) = ea c + eb (mirror folded in)
     __shared__ float efi[kRsEnt], efb[kRsEnt];      // 1 / a and b in float, for the estimate
@@ -254,18 +270,23 @@ adj_resample_kernel(const float* __restrict__ lbar, float* __restrict__ pbar,
     const int W = 2 * N;
     const int j0 = (blockIdx.x * kAdjThreads + threadIdx.x) * kRsBins;
     const float* ls = lbar + (size_t)s * 4 * N * W;
+    const Span sl{lbar, (long long)count * 4 * N * W, status};
+    const Span sp{pbar, (long long)count * K * M, status};
     float acc[kRsRows][kRsBins];
 #pragma unroll
     for (int r = 0; r < kRsRows; ++r)
 #pragma unroll
         for (int b = 0; b < kRsBins; ++b) acc[r][b] = 0.0f;
-    const int r0 = rptr[grp], r1 = rptr[grp + 1];
+    const int ngrp = (K + kRsRows - 1) / kRsRows;
+    const int r0 = in_bounds(status, grp, ngrp) ? rptr[grp] : 0;
+    const int r1 = in_bounds(status, grp, ngrp) ? rptr[grp + 1] : 0;
     for (int rb = r0; rb < r1; rb += kRsEnt) {
         const int ne = min(kRsEnt, r1 - rb);
         __syncthreads();                        // previous round's tables are read
         if (threadIdx.x < ne) {
-            const ReaderEntry en = rent[rb + threadIdx.x];
-            const int qi = en.code >> 1;
+            ReaderEntry en = {0, {0.0f, 0.0f, 0.0f, 0.0f}};
+            if (in_bounds(status, rb + threadIdx.x, n_ent)) en = rent[rb + threadIdx.x];
+            const int qi = in_bounds(status, en.code >> 1, 4LL * N) ? en.code >> 1 : 0;
             const RowGeom gm = geom[qi];
             long long a = gm.a_fx, b = gm.b_fx;
             if (en.code & 1) {                  // m' = (M - 1) - m = -a c + ((M - 1) - b)
@@ -297,7 +318,7 @@ adj_resample_kernel(const float* __restrict__ lbar, float* __restrict__ pbar,
             const float* lr = ls + (size_t)eq[e] * W + cs;
             float lv[kRsWin];
 #pragma unroll
-            for (int u = 0; u < kRsWin; ++u) lv[u] = cs + u <= ce ? lr[u] : 0.0f;
+            for (int u = 0; u < kRsWin; ++u) lv[u] = cs + u <= ce ? ld_in(sl, lr + u) : 0.0f;
             const long long mb = eb[e] + a * (long long)cs;
             float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;    // bins j0 .. j0 + 3
 #pragma unroll
@@ -332,7 +353,7 @@ adj_resample_kernel(const float* __restrict__ lbar, float* __restrict__ pbar,
         float* out = pbar + ((size_t)s * K + k) * M + j0;
 #pragma unroll
         for (int b = 0; b < kRsBins; ++b)
-            if (j0 + b < M) out[b] = acc[r][b];
+            if (j0 + b < M && sp.ok(out + b)) out[b] = acc[r][b];
     }
 }
 
@@ -366,11 +387,11 @@ cudaError_t launch_fht_adjoint(const fbp_plan_s* p, const float* img_grad, float
         const int left = launches - l;
         const int S = (k + left - 1) / left;
         switch (S) {
-            case 1: e = launch_af<1>(src, buf[cur], N, n, k, count, l == 0, resid_b, resid_w, st); break;
-            case 2: e = launch_af<2>(src, buf[cur], N, n, k, count, l == 0, resid_b, resid_w, st); break;
-            case 3: e = launch_af<3>(src, buf[cur], N, n, k, count, l == 0, resid_b, resid_w, st); break;
-            case 4: e = launch_af<4>(src, buf[cur], N, n, k, count, l == 0, resid_b, resid_w, st); break;
-            default: e = launch_af<5>(src, buf[cur], N, n, k, count, l == 0, resid_b, resid_w, st); break;
+            case 1: e = launch_af<1>(src, buf[cur], N, n, k, count, l == 0, resid_b, resid_w, p->d_status, st); break;
+            case 2: e = launch_af<2>(src, buf[cur], N, n, k, count, l == 0, resid_b, resid_w, p->d_status, st); break;
+            case 3: e = launch_af<3>(src, buf[cur], N, n, k, count, l == 0, resid_b, resid_w, p->d_status, st); break;
+            case 4: e = launch_af<4>(src, buf[cur], N, n, k, count, l == 0, resid_b, resid_w, p->d_status, st); break;
+            default: e = launch_af<5>(src, buf[cur], N, n, k, count, l == 0, resid_b, resid_w, p->d_status, st); break;
         }
         src = buf[cur];
         cur ^= 1;
@@ -386,7 +407,8 @@ cudaError_t launch_resample_adjoint(const fbp_plan_s* p, const float* lin_grad, 
     const int per_cta = kAdjThreads * kRsBins;
     const dim3 grid((p->M + per_cta - 1) / per_cta, (p->K + kRsRows - 1) / kRsRows, count);
     adj_resample_kernel<<<grid, kAdjThreads, 0, st>>>(lin_grad, filt_grad, p->d_geom, p->d_readers,
-                                                      p->d_reader_ent, p->N, p->K, p->M);
+                                                      p->d_reader_ent, p->N, p->K, p->M, count,
+                                                      p->n_reader_ent, p->d_status);
     return cudaGetLastError();
 }
 

@@ -95,6 +95,27 @@ using bf16 = __nv_bfloat16;
 
 __device__ int g_cnn_status;       // FBP_ERR_TIMEOUT after an expired wait, else 0
 
+// Range checks of the bounds-checked build (FBP_BOUNDS_CHECK): an index outside its buffer
+// records FBP_ERR_INTERNAL in the corrector's status word and the access is skipped (a
+// skipped load reads 0; a skipped bulk copy leaves its stage unfilled, so the wait for it
+// expires and the CTA stops).  In the normal build every check is true and compiles away.
+__device__ __forceinline__ bool cnn_ok(long long i, long long n)
+{
+    return in_bounds(&g_cnn_status, i, n);
+}
+
+// [i, i + len) inside [0, n)
+__device__ __forceinline__ bool cnn_span_ok(long long i, long long len, long long n)
+{
+    return cnn_ok(i, n) && cnn_ok(i + len - 1, n);
+}
+
+#ifdef FBP_BOUNDS_CHECK
+// Test hook (fbp_check_cnn_image_limit): when > 0, the last layer checks its image loads and
+// stores against this many images instead of the call's count.
+__device__ int g_cnn_image_limit;
+#endif
+
 // Geometry of the record layout for N x N images.
 struct ActGeom {
     int N, W, T;                  // image size, padded row length, tensor-core tiles per image
@@ -351,7 +372,8 @@ __global__ void cnn_prep_weights_kernel(const float* __restrict__ w, bf16* __res
     if (chunk >= kWChunks) {
         const int q = row / 32, dx = (row % 32) / 8, ol = row % 8;
         const bool part = chunk == kWChunks && dx == 0 && c8 < 3;
-        fwd[e] = __float2bfloat16_rn(part ? bf16_part(w[kC * kC * kTaps + 8 * q + ol], c8) : 0.0f);
+        const int bi = kC * kC * kTaps + 8 * q + ol;               // bias of output channel 8q + ol
+        fwd[e] = __float2bfloat16_rn(part && cnn_ok(bi, kC * kC * kTaps + kC) ? bf16_part(w[bi], c8) : 0.0f);
         bwd[e] = __float2bfloat16_rn(0.0f);
         return;
     }
@@ -360,8 +382,10 @@ __global__ void cnn_prep_weights_kernel(const float* __restrict__ w, bf16* __res
     const int o = 8 * q + ol;
     float vf = 0.0f, vb = 0.0f;
     if (dx < 3) {
-        vf = w[((o * kC + cin) * 3 + dy) * 3 + dx];              // W[o][cin][dy][dx]
-        vb = w[((cin * kC + o) * 3 + (2 - dy)) * 3 + (2 - dx)];  // W[cin][o][2-dy][2-dx]
+        const int fi = ((o * kC + cin) * 3 + dy) * 3 + dx;              // W[o][cin][dy][dx]
+        const int bi = ((cin * kC + o) * 3 + (2 - dy)) * 3 + (2 - dx);  // W[cin][o][2-dy][2-dx]
+        if (cnn_ok(fi, kC * kC * kTaps)) vf = w[fi];
+        if (cnn_ok(bi, kC * kC * kTaps)) vb = w[bi];
     }
     fwd[e] = __float2bfloat16_rn(vf);
     bwd[e] = __float2bfloat16_rn(vb);
@@ -388,7 +412,8 @@ __global__ void cnn_prep_last_kernel(const float* __restrict__ w, bf16* __restri
     const int q = row / 32, dx = (row % 32) / 8, part = row % 8;
     float v = 0.0f;
     (void)q;
-    if (dx < 3 && part < 3) v = bf16_part(w[(cin * 3 + dy) * 3 + dx], part);
+    if (dx < 3 && part < 3 && cnn_ok((cin * 3 + dy) * 3 + dx, kC * kTaps))
+        v = bf16_part(w[(cin * 3 + dy) * 3 + dx], part);
     img[e] = __float2bfloat16_rn(v);
 }
 
@@ -484,7 +509,8 @@ cnn_conv32_kernel(ConvArgs a)
                 for (int dy = 0; dy < 3; ++dy) {
                     const long long r0 = m0 + (long long)(dy - 1) * G.W - 1;     // run start
                     const uint4* src = a.in + ((long long)img * G.plane + r0) * kPlanes;
-                    bulk_g2s(dst + dy * kRunBytes + (int)(r0 & 7) * kRecBytes, src, kRunCopy, full + s);
+                    if (cnn_span_ok(r0, kRunCopy / kRecBytes, G.plane) && cnn_ok(img, a.images))
+                        bulk_g2s(dst + dy * kRunBytes + (int)(r0 & 7) * kRecBytes, src, kRunCopy, full + s);
                 }
             }
             // copies still in flight land before the CTA exits
@@ -554,8 +580,8 @@ cnn_conv32_kernel(ConvArgs a)
             const int part = (int)(z - rec * kPlanes);
             const long long im = rec / (head + tail);
             const long long r = rec - im * (head + tail);
-            a.out[(im * G.plane + (r < head ? r : tail0 + (r - head))) * kPlanes + part] =
-                make_uint4(0u, 0u, 0u, 0u);
+            const long long o = (im * G.plane + (r < head ? r : tail0 + (r - head))) * kPlanes + part;
+            if (cnn_ok(o, (long long)a.images * G.plane * kPlanes)) a.out[o] = make_uint4(0u, 0u, 0u, 0u);
         }
         // TMEM lane 32q + 8dx + g holds output channel 8q + g at tap dx (dx = 3: zero rows).
         // With the 16x256b loads lane t of the warp holds, for g = t / 4 and every group of 8
@@ -588,7 +614,12 @@ cnn_conv32_kernel(ConvArgs a)
                 const bool ok = lane < 16 && px < kTileOut && (unsigned)y < (unsigned)a.N &&
                                 (unsigned)x < (unsigned)a.N;
                 const size_t pix = ok ? ((size_t)img * a.N + y) * a.N + x : 0;
-                const float xin = ok ? __ldg(a.ximg + pix) : 0.0f;
+                long long npx = (long long)a.images * a.N * a.N;
+#ifdef FBP_BOUNDS_CHECK
+                if (g_cnn_image_limit > 0 && g_cnn_image_limit < a.images)
+                    npx = (long long)g_cnn_image_limit * a.N * a.N;
+#endif
+                const float xin = ok && cnn_ok((long long)pix, npx) ? __ldg(a.ximg + pix) : 0.0f;
                 if (!wait_bar(tfull + b, j & 1u, abort_flag)) break;
                 tc_fence_after();
                 const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kNpix + 8 * r0);
@@ -628,7 +659,7 @@ cnn_conv32_kernel(ConvArgs a)
                     }
                 }
                 __syncwarp();
-                if (ok) a.yimg[pix] = xin + (vs[lane] + bias);
+                if (ok && cnn_ok((long long)pix, npx)) a.yimg[pix] = xin + (vs[lane] + bias);
                 __syncwarp();
                 continue;
             }
@@ -700,8 +731,9 @@ cnn_conv32_kernel(ConvArgs a)
                 if (px < kTileOut) {
                     const bool inside = (unsigned)y < (unsigned)a.N && (unsigned)x < (unsigned)a.N;
                     const long long rec = ((long long)img * G.plane + mrec) * kPlanes + chunk_pos(mrec, q);
+                    const bool rec_in = cnn_ok(rec, (long long)a.images * G.plane * kPlanes);
                     if (MASK && inside) {
-                        const uint4 mr = a.mask[rec];
+                        const uint4 mr = rec_in ? a.mask[rec] : make_uint4(0u, 0u, 0u, 0u);
                         const uint32_t mw[4] = {mr.x, mr.y, mr.z, mr.w};
 #pragma unroll
                         for (int hh = 0; hh < 4; ++hh) {
@@ -710,7 +742,8 @@ cnn_conv32_kernel(ConvArgs a)
                             w4[hh] &= keep;
                         }
                     }
-                    a.out[rec] = inside ? make_uint4(w4[0], w4[1], w4[2], w4[3]) : make_uint4(0u, 0u, 0u, 0u);
+                    if (rec_in)
+                        a.out[rec] = inside ? make_uint4(w4[0], w4[1], w4[2], w4[3]) : make_uint4(0u, 0u, 0u, 0u);
                 }
             }
         }
@@ -816,12 +849,14 @@ cnn_wgrad_tc_kernel(const uint4* __restrict__ gz, const uint4* __restrict__ h, f
                 unsigned char* st = stages + (size_t)s * kWgStageBytes;
                 mbar_expect_tx(full + s, kWgARec * kRecBytes + 3 * kWgTile * kRecBytes);
                 const long long ra = m0 - 1;                         // A run start
-                bulk_g2s(st + (int)(ra & 7) * kRecBytes, h + (base + ra) * kPlanes, kWgARec * kRecBytes, full + s);
+                if (cnn_span_ok(ra, kWgARec, G.plane) && cnn_ok(img, images))
+                    bulk_g2s(st + (int)(ra & 7) * kRecBytes, h + (base + ra) * kPlanes, kWgARec * kRecBytes, full + s);
                 unsigned char* bb = st + kWgABytes + (int)((m0 + G.W) & 7) * kRecBytes;
 #pragma unroll 1
                 for (int dy = 0; dy < 3; ++dy) {
                     const long long rb = m0 - (long long)(dy - 1) * G.W;
-                    bulk_g2s(bb + (size_t)dy * L, gz + (base + rb) * kPlanes, kWgTile * kRecBytes, full + s);
+                    if (cnn_span_ok(rb, kWgTile, G.plane) && cnn_ok(img, images))
+                        bulk_g2s(bb + (size_t)dy * L, gz + (base + rb) * kPlanes, kWgTile * kRecBytes, full + s);
                 }
             }
             for (long long j = i - kWgStages; j < i; ++j)
@@ -873,8 +908,10 @@ cnn_wgrad_tc_kernel(const uint4* __restrict__ gz, const uint4* __restrict__ h, f
                 tmem_wait_ld();
                 const int dy = c0 / 32, c = lane;
 #pragma unroll
-                for (int o = 0; o < 32; ++o)
-                    atomicAdd(gw + ((size_t)(o * kC + c) * 3 + dy) * 3 + q, __uint_as_float(v[o]));
+                for (int o = 0; o < 32; ++o) {
+                    const long long gi = ((long long)(o * kC + c) * 3 + dy) * 3 + q;
+                    if (cnn_ok(gi, kC * kC * kTaps)) atomicAdd(gw + gi, __uint_as_float(v[o]));
+                }
             }
         }
     }
@@ -901,7 +938,10 @@ cnn_bias_grad_kernel(const uint4* __restrict__ gz, float* __restrict__ gb, long 
          r += (long long)gridDim.x * blockDim.x) {
         float v[kC];
 #pragma unroll
-        for (int p = 0; p < kPlanes; ++p) unpack_record(gz[r * kPlanes + chunk_pos(r, p)], v + 8 * p);
+        for (int p = 0; p < kPlanes; ++p) {
+            const long long gi = r * kPlanes + chunk_pos(r, p);
+            unpack_record(cnn_ok(gi, records * kPlanes) ? gz[gi] : make_uint4(0u, 0u, 0u, 0u), v + 8 * p);
+        }
 #pragma unroll
         for (int c = 0; c < kC; ++c) acc[c] += v[c];
     }
@@ -944,6 +984,7 @@ cnn_first_kernel(const float* __restrict__ x, const float* __restrict__ w,
     const ActGeom G = act_geom(N);
     const int y = blockIdx.y, img = blockIdx.z;
     uint4* dst = h + (long long)img * G.plane * kPlanes;
+    const long long dst_n = G.plane * kPlanes;             // this image's record chunks
     const uint4 zero4 = make_uint4(0u, 0u, 0u, 0u);
     if (y == N) {
         // records outside every image row: [0, kRecGuard + W) and [kRecGuard + (N+1) W, plane)
@@ -953,7 +994,8 @@ cnn_first_kernel(const float* __restrict__ x, const float* __restrict__ w,
         for (long long z = (long long)blockIdx.x * blockDim.x + threadIdx.x; z < n;
              z += (long long)gridDim.x * blockDim.x) {
             const long long r = z / kPlanes;
-            dst[(r < head ? r : tail0 + (r - head)) * kPlanes + (int)(z - r * kPlanes)] = zero4;
+            const long long o = (r < head ? r : tail0 + (r - head)) * kPlanes + (int)(z - r * kPlanes);
+            if (cnn_ok(o, dst_n)) dst[o] = zero4;
         }
         return;
     }
@@ -962,10 +1004,12 @@ cnn_first_kernel(const float* __restrict__ x, const float* __restrict__ w,
     const long long rrow = rec_index(G, y, 0);               // record of pixel (y, 0)
     if (x0 == 0)
 #pragma unroll
-        for (int p = 0; p < kPlanes; ++p) dst[(rrow - 1) * kPlanes + p] = zero4;
+        for (int p = 0; p < kPlanes; ++p)
+            if (cnn_ok((rrow - 1) * kPlanes + p, dst_n)) dst[(rrow - 1) * kPlanes + p] = zero4;
     if (x0 + kFirstPx == N)
 #pragma unroll
-        for (int p = 0; p < kPlanes; ++p) dst[(rrow + N) * kPlanes + p] = zero4;
+        for (int p = 0; p < kPlanes; ++p)
+            if (cnn_ok((rrow + N) * kPlanes + p, dst_n)) dst[(rrow + N) * kPlanes + p] = zero4;
     const bool live = x0 < N;
     uint4* mine = stage + threadIdx.x * kFirstStage;
     // window xv[dy][k] = x(y + dy - 1, x0 + k - 1), k = 0..5, zero outside the image
@@ -974,7 +1018,9 @@ cnn_first_kernel(const float* __restrict__ x, const float* __restrict__ w,
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy) {
         const int yy = y + dy - 1;
-        if (live && (unsigned)yy < (unsigned)N) {
+        if (live && (unsigned)yy < (unsigned)N &&
+            cnn_span_ok((long long)yy * N + x0 - (x0 > 0 ? 1 : 0), kFirstPx + (x0 > 0) + (x0 + kFirstPx < N),
+                        (long long)N * N)) {
             const float* row = xs + (size_t)yy * N;
             const float4 mid = *reinterpret_cast<const float4*>(row + x0);
             xv[dy][0] = x0 > 0 ? row[x0 - 1] : 0.0f;
@@ -1032,7 +1078,8 @@ cnn_first_kernel(const float* __restrict__ x, const float* __restrict__ w,
     const int nw = min(N - sx0, kFirstPx * kFirstThreads) * kPlanes;
     uint4* out = dst + (rrow + sx0) * kPlanes;
     for (int e = threadIdx.x; e < nw; e += kFirstThreads)
-        out[e] = stage[(e / (kFirstPx * kPlanes)) * kFirstStage + e % (kFirstPx * kPlanes)];
+        if (cnn_ok((rrow + sx0) * kPlanes + e, dst_n))
+            out[e] = stage[(e / (kFirstPx * kPlanes)) * kFirstStage + e % (kFirstPx * kPlanes)];
 }
 
 // the 32 channels of record r of one image's records
@@ -1064,6 +1111,7 @@ cnn_last_backward_kernel(const float* __restrict__ gy, const uint4* __restrict__
     }
     const long long ib = (long long)blockIdx.y * G.plane * kPlanes;
     uint4* dst = g + ib + r * kPlanes;
+    if (!cnn_span_ok(r * kPlanes, kPlanes, G.plane * kPlanes)) return;
     if ((unsigned)py >= (unsigned)N || (unsigned)px >= (unsigned)N) {
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) dst[p] = make_uint4(0u, 0u, 0u, 0u);
@@ -1074,7 +1122,8 @@ cnn_last_backward_kernel(const float* __restrict__ gy, const uint4* __restrict__
 #pragma unroll
     for (int tap = 0; tap < kTaps; ++tap) {
         const int yy = py - (tap / 3 - 1), xx = px - (tap % 3 - 1);
-        v[tap] = (yy >= 0 && yy < N && xx >= 0 && xx < N) ? gy[img + (size_t)yy * N + xx] : 0.0f;
+        v[tap] = (yy >= 0 && yy < N && xx >= 0 && xx < N && cnn_ok((long long)yy * N + xx, (long long)N * N))
+                     ? gy[img + (size_t)yy * N + xx] : 0.0f;
     }
     float m[kC];
     load_pixel32(m, h5 + ib, r);
@@ -1137,7 +1186,8 @@ cnn_wgrad_thin_kernel(const uint4* __restrict__ wide, const float* __restrict__ 
             const long long r = WIDE_IS_GZ ? rec_index(G, y0 + pix / kTileX, x0 + pix % kTileX)
                                            : rec_index(G, y0 - 1 + pix / kHaloX, x0 - 1 + pix % kHaloX);
             float v[8];
-            unpack_record(wi[r * kPlanes + chunk_pos(r, ch)], v);
+            const long long wix = r * kPlanes + chunk_pos(r, ch);
+            unpack_record(cnn_ok(wix, G.plane * kPlanes) ? wi[wix] : make_uint4(0u, 0u, 0u, 0u), v);
             *reinterpret_cast<float4*>(&ws[pix][8 * ch]) = make_float4(v[0], v[1], v[2], v[3]);
             *reinterpret_cast<float4*>(&ws[pix][8 * ch + 4]) = make_float4(v[4], v[5], v[6], v[7]);
         }
@@ -1145,9 +1195,11 @@ cnn_wgrad_thin_kernel(const uint4* __restrict__ wide, const float* __restrict__ 
             float v;
             if (WIDE_IS_GZ) {
                 const int gy = y0 - 1 + e / kHaloX, gx = x0 - 1 + e % kHaloX;
-                v = (gy >= 0 && gy < N && gx >= 0 && gx < N) ? ti[(size_t)gy * N + gx] : 0.0f;
+                v = (gy >= 0 && gy < N && gx >= 0 && gx < N && cnn_ok((long long)gy * N + gx, (long long)N * N))
+                        ? ti[(size_t)gy * N + gx] : 0.0f;
             } else {
-                v = ti[(size_t)(y0 + e / kTileX) * N + x0 + e % kTileX];
+                const long long ti_i = (long long)(y0 + e / kTileX) * N + x0 + e % kTileX;
+                v = cnn_ok(ti_i, (long long)N * N) ? ti[ti_i] : 0.0f;
             }
             ts[e] = v;
         }
@@ -1417,6 +1469,18 @@ fbp_status fbp_cnn_backward(const float* d_params, const float* d_x, const float
     return fbp::cnn::backward(d_params, d_x, d_gy, d_gparams, d_ws, N, batch, sms,
                               (cudaStream_t)stream) == cudaSuccess ? FBP_OK : FBP_ERR_CUDA;
 }
+
+#ifdef FBP_BOUNDS_CHECK
+#include "../../include/fbp_check.h"
+
+fbp_status fbp_check_cnn_image_limit(int images)
+{
+    if (images < 0) return FBP_ERR_INVALID_ARG;
+    if (cudaDeviceSynchronize() != cudaSuccess) return FBP_ERR_CUDA;
+    return cudaMemcpyToSymbol(fbp::g_cnn_image_limit, &images, sizeof(int)) == cudaSuccess ? FBP_OK
+                                                                                           : FBP_ERR_CUDA;
+}
+#endif
 
 fbp_status fbp_cnn_last_error(void)
 {

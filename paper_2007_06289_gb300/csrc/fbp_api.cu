@@ -643,6 +643,7 @@ fbp_status fbp_plan(fbp_plan_t* out, int N, int K, int M, int batch,
         trig[k] = make_float2((float)cos(th), (float)sin(th));
     }
     const ReaderTable readers = build_readers(geo, K);
+    p->n_reader_ent = (int)readers.ent.size();
     cudaError_t e = cudaMalloc(&p->d_geom, geo.size() * sizeof(fbp::RowGeom));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_trig, trig.size() * sizeof(float2));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_readers, readers.ptr.size() * sizeof(int));

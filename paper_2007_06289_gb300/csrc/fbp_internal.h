@@ -96,6 +96,12 @@ __device__ __forceinline__ float ldg_in(const Span& s, const float* p)
     return s.ok(p) ? __ldg(p) : 0.0f;
 }
 
+// The same as a plain load (no read-only cache path): 0 outside the region.
+__device__ __forceinline__ float ld_in(const Span& s, const float* p)
+{
+    return s.ok(p) ? *p : 0.0f;
+}
+
 // A geometry row names angle rows inside the sinogram: k0 in [0, K), and the second angle
 // row k0 + 1 < K unless the row wraps (k0 = K - 1, second row = row 0 mirrored).
 __host__ __device__ inline bool row_geom_valid(const RowGeom& g, int K)
@@ -136,6 +142,7 @@ struct fbp_plan_s {
     int* d_readers;         // transposed-resampling table, per group of kRsRows sinogram
                             // rows: [groups + 1] CSR offsets into d_reader_ent
     fbp::ReaderEntry* d_reader_ent;
+    int n_reader_ent;       // entries of d_reader_ent
     float2* d_hough_w;      // [4][N]: ((1 - ft), ft) / sqrt(1 + sigma^2), Hough-space data
     fbp::RadonRow* d_radon; // [K]: the fast Radon transform's resampling
     float* d_sirt;          // SIRT tables of one slice, made on first use: R^-1 [4][N][2N],

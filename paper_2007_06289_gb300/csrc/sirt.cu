@@ -16,10 +16,11 @@ namespace {
 
 constexpr int kSirtThreads = 256;
 
-// value of detector bin j of a sinogram row, zero outside [0, M)
-__device__ __forceinline__ float bin_or_zero(const float* row, int M, int j)
+// value of detector bin j of a sinogram row, zero outside [0, M) (and, in the bounds-checked
+// build, outside the sinogram buffer)
+__device__ __forceinline__ float bin_or_zero(const Span& sp, const float* row, int M, int j)
 {
-    return (j >= 0 && j < M) ? row[j] : 0.0f;
+    return (j >= 0 && j < M) ? ld_in(sp, row + j) : 0.0f;
 }
 
 // b[q][i][c] = hw.x * lerp(row k0) + hw.y * lerp(row k0 + 1, or row 0 mirrored past the last
@@ -27,17 +28,20 @@ __device__ __forceinline__ float bin_or_zero(const float* row, int M, int j)
 __global__ void __launch_bounds__(kSirtThreads)
 hough_data_kernel(const float* __restrict__ sino, float* __restrict__ lin,
                   const RowGeom* __restrict__ geom, const float2* __restrict__ hw, int N, int K,
-                  int M, int* status)
+                  int M, int count, int* status)
 {
     const int W = 2 * N;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     const int qi = blockIdx.y;                  // q * N + i
     const int s = blockIdx.z;
     if (c >= W) return;
+    const Span sp{sino, (long long)count * K * M, status};
+    const long long o = ((long long)s * 4 * N + qi) * W + c;
+    if (!in_bounds(status, o, (long long)count * 4 * N * W)) return;
     const RowGeom gm = geom[qi];
     if (!row_geom_valid(gm, K)) {               // rejected geometry row: zeros
         if (c == 0) flag_status(status, (int)FBP_ERR_INTERNAL);
-        lin[((size_t)s * 4 * N + qi) * W + c] = 0.0f;
+        lin[o] = 0.0f;
         return;
     }
     const float2 w = hw[qi];
@@ -46,21 +50,21 @@ hough_data_kernel(const float* __restrict__ sino, float* __restrict__ lin,
     const int j = (int)(m >> kFixBits);
     const float f = __uint2float_rn((unsigned)m) * 0x1p-32f;
     const float* ra = ps + (size_t)gm.k0 * M;
-    const float a0 = bin_or_zero(ra, M, j), a1 = bin_or_zero(ra, M, j + 1);
+    const float a0 = bin_or_zero(sp, ra, M, j), a1 = bin_or_zero(sp, ra, M, j + 1);
     const float va = fmaf(f, a1 - a0, a0);
     float vb;
     if (!gm.wrap) {
         const float* rb = ra + M;
-        const float b0 = bin_or_zero(rb, M, j), b1 = bin_or_zero(rb, M, j + 1);
+        const float b0 = bin_or_zero(sp, rb, M, j), b1 = bin_or_zero(sp, rb, M, j + 1);
         vb = fmaf(f, b1 - b0, b0);
     } else {
         const long long mm = ((long long)(M - 1) << kFixBits) - m;
         const int jm = (int)(mm >> kFixBits);
         const float fm = __uint2float_rn((unsigned)mm) * 0x1p-32f;
-        const float b0 = bin_or_zero(ps, M, jm), b1 = bin_or_zero(ps, M, jm + 1);
+        const float b0 = bin_or_zero(sp, ps, M, jm), b1 = bin_or_zero(sp, ps, M, jm + 1);
         vb = fmaf(fm, b1 - b0, b0);
     }
-    lin[((size_t)s * 4 * N + qi) * W + c] = fmaf(w.y, vb, w.x * va);
+    lin[o] = fmaf(w.y, vb, w.x * va);
 }
 
 // Fast Radon transform: sinogram row k from the dyadic line sums H of its line class, the
@@ -68,14 +72,17 @@ hough_data_kernel(const float* __restrict__ sino, float* __restrict__ lin,
 // the column, zero outside [0, 2N)), mixed (1 - t, t), times the path length per row.
 __global__ void __launch_bounds__(kSirtThreads)
 radon_kernel(const float* __restrict__ lin, float* __restrict__ sino,
-             const RadonRow* __restrict__ rows, int N, int K, int M)
+             const RadonRow* __restrict__ rows, int N, int K, int M, int count, int* status)
 {
     const int W = 2 * N;
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = blockIdx.y;
     const int s = blockIdx.z;
     if (m >= M) return;
+    const long long o = ((long long)s * K + k) * M + m;
+    if (!in_bounds(status, o, (long long)count * K * M)) return;
     const RadonRow e = rows[k];
+    const Span sl{lin, (long long)count * 4 * N * W, status};
     const float* h = lin + (((size_t)s * 4 + e.q) * N + e.i0) * W;
     float v[2];
 #pragma unroll
@@ -84,11 +91,11 @@ radon_kernel(const float* __restrict__ lin, float* __restrict__ sino,
         const int c = (int)(cf >> kFixBits);
         const float f = __uint2float_rn((unsigned)cf) * 0x1p-32f;
         const float* row = h + (size_t)j * W;
-        const float h0 = (c >= 0 && c < W) ? row[c] : 0.0f;
-        const float h1 = (c + 1 >= 0 && c + 1 < W) ? row[c + 1] : 0.0f;
+        const float h0 = (c >= 0 && c < W) ? ld_in(sl, row + c) : 0.0f;
+        const float h1 = (c + 1 >= 0 && c + 1 < W) ? ld_in(sl, row + c + 1) : 0.0f;
         v[j] = fmaf(f, h1, (1.0f - f) * h0);
     }
-    sino[((size_t)s * K + k) * M + m] = fmaf(e.t, v[1], (1.0f - e.t) * v[0]) * e.scale;
+    sino[o] = fmaf(e.t, v[1], (1.0f - e.t) * v[0]) * e.scale;
 }
 
 // f = f + lam * cinv * t
@@ -135,7 +142,7 @@ cudaError_t launch_hough_data(const fbp_plan_s* p, const float* sino, float* lin
     if (count <= 0) return cudaSuccess;
     const dim3 grid((2 * p->N + kSirtThreads - 1) / kSirtThreads, 4 * p->N, count);
     hough_data_kernel<<<grid, kSirtThreads, 0, st>>>(sino, lin, p->d_geom, p->d_hough_w, p->N,
-                                                     p->K, p->M, p->d_status);
+                                                     p->K, p->M, count, p->d_status);
     return cudaGetLastError();
 }
 
@@ -144,7 +151,8 @@ cudaError_t launch_radon(const fbp_plan_s* p, const float* lin, float* sino, int
 {
     if (count <= 0) return cudaSuccess;
     const dim3 grid((p->M + kSirtThreads - 1) / kSirtThreads, p->K, count);
-    radon_kernel<<<grid, kSirtThreads, 0, st>>>(lin, sino, p->d_radon, p->N, p->K, p->M);
+    radon_kernel<<<grid, kSirtThreads, 0, st>>>(lin, sino, p->d_radon, p->N, p->K, p->M, count,
+                                                p->d_status);
     return cudaGetLastError();
 }
 

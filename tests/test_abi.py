@@ -95,7 +95,8 @@ def test_checked_library_exports_the_abi_and_its_test_hook(fbp):
     path = build.build(bounds_check=True)
     checked = ctypes.CDLL(path)
     hooks = fbp.header_functions(fbp.CHECK_HEADER)
-    assert hooks == ["fbp_check_set_row_angle"]
+    assert hooks == ["fbp_check_cnn_image_limit", "fbp_check_set_row_angle"]
     for name in fbp.header_functions() + hooks:
         assert hasattr(checked, name), name
-    assert not hasattr(fbp.load_library(), "fbp_check_set_row_angle")
+    for name in hooks:
+        assert not hasattr(fbp.load_library(), name), name

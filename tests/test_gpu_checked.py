@@ -2,6 +2,7 @@
 with FBP_LIBRARY pointing at it -- small parity cases with every access range-checked and
 the status word clear afterwards, then a rejected geometry row setting the status word."""
 import os
+import re
 import subprocess
 import sys
 
@@ -20,3 +21,6 @@ def test_checked_library_cases():
                         os.path.join("tests", "checked_cases.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=1200)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
+    # every case ran and passed: none skipped or deselected
+    summary = r.stdout.strip().splitlines()[-1]
+    assert re.match(r"^\d+ passed(, \d+ warnings?)? in ", summary), summary
