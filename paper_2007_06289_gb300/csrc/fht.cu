@@ -685,10 +685,13 @@ __device__ __forceinline__ void bar_wait(uint64_t* bar, int* status)
 // (F_- + F_+), and either stores the sum into the image (v quarters: [y = tau][x = u]) or
 // adds it to the image through a shared-memory transpose (h quarters: [y = u][x = tau]).
 // Launched for the v quarters first and the h quarters second, so each pixel ends as
-// (F_v- + F_v+) + (F_h- + F_h+).  Both quarters' rows are requested up front (one bulk
-// copy per row that lies wholly inside its stored range, counted on the quarter's mbarrier;
-// 16-byte asynchronous copies with zero fill for the rows at the ends of the range), so the
-// second quarter's copies run behind the first quarter's stages.
+// (F_v- + F_v+) + (F_h- + F_h+).  Each h CTA asks L2 for its image rows when it starts, so
+// that the read-modify-write at its end finds them there, and the h launch takes the slices
+// in reverse order, starting on the images the v launch wrote last.  Both quarters' rows
+// are requested up front (one bulk copy per row that lies wholly inside its stored range,
+// counted on the quarter's mbarrier; 16-byte asynchronous copies with zero fill for the
+// rows at the ends of the range), so the second quarter's copies run behind the first
+// quarter's stages.
 template <int LOGR2, int T2, bool HORIZ>
 __global__ void __launch_bounds__(kNT2, 3)
 pass2_kernel(Pass2Args a)
@@ -708,11 +711,16 @@ pass2_kernel(Pass2Args a)
     const int x0 = blockIdx.x * T2;            // the last tile may run past N
     const int nx = min(T2, N - x0);            // intercepts of this tile inside the image
     const int tau_hi = blockIdx.y;
-    const int s = blockIdx.z;
+    const int s = HORIZ ? (int)gridDim.z - 1 - (int)blockIdx.z : (int)blockIdx.z;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* img = a.img_tab ? a.img_tab[s] : a.img + (size_t)s * N * N;
     const Span gs{a.g, a.g_n, a.status};
     const Span is{img, (long long)N * N, a.status};    // this slice's image
+    if constexpr (HORIZ) {
+        // image row x0 + t, columns tau_hi R .. tau_hi R + R - 1 (at most one 128-byte line)
+        const float* ir = img + (size_t)(x0 + (int)threadIdx.x) * N + tau_hi * R;
+        if ((int)threadIdx.x < nx && is.ok(ir)) asm volatile("prefetch.global.L2 [%0];" ::"l"(ir));
+    }
     __shared__ uint64_t rows_landed[2];                // per quarter: its bulk row copies
     if (threadIdx.x == 0) {
         bar_init(&rows_landed[0]);
