@@ -364,10 +364,11 @@ def run_ours(args):
     fbp.fbp_reconstruct_host(plan, h_sino, h_img)
     torch.cuda.synchronize(dev)
     # The copies bound this path (~210 GB/s host to device on this machine) and their rate
-    # varies with what else the host is doing: three timed runs, the median reported.
+    # varies with what else the host is doing (single runs at twice the time): five timed
+    # runs, the median reported.
     e2e_steps = max(1, min(args.steps, 10))
     e2e_runs = []
-    for _ in range(3):
+    for _ in range(5):
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         for _ in range(e2e_steps):
