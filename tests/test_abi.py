@@ -100,3 +100,8 @@ def test_checked_library_exports_the_abi_and_its_test_hook(fbp):
         assert hasattr(checked, name), name
     for name in hooks:
         assert not hasattr(fbp.load_library(), name), name
+    # argument checks come before any CUDA call: FBP_ERR_INVALID_ARG without a GPU
+    checked.fbp_check_cnn_image_limit.argtypes = [ctypes.c_int]
+    checked.fbp_check_set_row_angle.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    assert checked.fbp_check_cnn_image_limit(-1) == 1
+    assert checked.fbp_check_set_row_angle(None, 0, 0, 0) == 1
