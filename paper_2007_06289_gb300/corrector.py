@@ -8,6 +8,7 @@ optimisers can train them, and a small training loop.
 from __future__ import annotations
 
 import math
+import warnings
 
 import numpy as np
 import torch
@@ -74,11 +75,25 @@ def correct(params: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
     return _CorrectorFn.apply(params, x)
 
 
-def infer(params: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
-    """Inference without keeping activations."""
+def infer(params: torch.Tensor, x: torch.Tensor, fallback: bool = False) -> torch.Tensor:
+    """Inference without keeping activations.
+
+    fallback=True: read the corrector's status word after the call (this synchronises the
+    device).  If it is not clear -- a bounded wait in the corrector's kernels expired, or in
+    the bounds-checked library a range check failed -- the output cannot be trusted, and the
+    plain fast reconstruction x itself is returned (a copy, with a warning): the method
+    without its corrector.  The status word is the process's, shared by every corrector
+    call, so concurrent calls on other streams can trip it too."""
     B, N = x.shape[0], x.shape[-1]
     y = torch.empty_like(x)
-    fbp.fbp_cnn_forward(params, x.contiguous(), y, _WS.get(N, B, False, x.device), train=False)
+    xc = x.contiguous()
+    fbp.fbp_cnn_forward(params, xc, y, _WS.get(N, B, False, x.device), train=False)
+    if fallback:
+        status = fbp.fbp_cnn_last_error()
+        if status != 0:
+            warnings.warn(f"corrector status {status} ({fbp.fbp_status_str(status)}): "
+                          "returning the uncorrected fast reconstruction", RuntimeWarning)
+            return xc.clone()
     return y
 
 
