@@ -247,8 +247,11 @@ fbp_status fbp_cnn_backward(const float* d_params, const float* d_x, const float
 
 /* Synchronise the current device and read (then clear) the corrector's device status word:
  * FBP_ERR_TIMEOUT if a tensor-core convolution gave up a bounded wait (about a second) for
- * its copies or its matrix products since the last read -- its output is then incomplete --
- * else FBP_OK.  FBP_ERR_CUDA if the device cannot be read. */
+ * its copies or its matrix products since the last read -- its output is then incomplete --;
+ * in the library built with FBP_BOUNDS_CHECK (libfbp_checked.so), FBP_ERR_INTERNAL if a
+ * corrector kernel formed an index or a bulk-copy range outside its buffer (the access is
+ * skipped); else FBP_OK.  The first code recorded wins.  FBP_ERR_CUDA if the device cannot
+ * be read. */
 fbp_status fbp_cnn_last_error(void);
 
 /* ------------------------------------------------------------------ ragged volumes
@@ -365,10 +368,11 @@ const char* fbp_status_str(fbp_status status);
  * FBP_ERR_INTERNAL when a kernel rejected a geometry-table row naming an angle row outside
  * the sinogram (checked in every build; the row is resampled as zeros) or, in the library
  * built with FBP_BOUNDS_CHECK (libfbp_checked.so, include/fbp_check.h), an index outside its
- * buffer or Hough tile (the access is skipped); FBP_ERR_TIMEOUT when a second-pass CTA gave
- * up its bounded wait (about a second) for its bulk row copies (its output tile is then
- * wrong); FBP_OK if none since the last read.  The corrector's bounded waits report through
- * fbp_cnn_last_error. */
+ * buffer or Hough tile in a kernel of the reconstruction, its adjoints, the Hough-space
+ * data, the fast Radon transform or SIRT (the access is skipped); FBP_ERR_TIMEOUT when a
+ * second-pass CTA gave up its bounded wait (about a second) for its bulk row copies (its
+ * output tile is then wrong); FBP_OK if none since the last read.  The corrector's kernels
+ * report through fbp_cnn_last_error. */
 fbp_status fbp_last_device_error(fbp_plan_t plan);
 
 #ifdef __cplusplus
