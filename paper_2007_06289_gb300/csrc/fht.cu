@@ -717,7 +717,8 @@ pass2_kernel(Pass2Args a)
     const Span gs{a.g, a.g_n, a.status};
     const Span is{img, (long long)N * N, a.status};    // this slice's image
     if constexpr (HORIZ) {
-        // image row x0 + t, columns tau_hi R .. tau_hi R + R - 1 (at most one 128-byte line)
+        // image row x0 + t from column tau_hi R on: the first 128-byte line of its R columns
+        // (all of them while R <= 32)
         const float* ir = img + (size_t)(x0 + (int)threadIdx.x) * N + tau_hi * R;
         if ((int)threadIdx.x < nx && is.ok(ir)) asm volatile("prefetch.global.L2 [%0];" ::"l"(ir));
     }
